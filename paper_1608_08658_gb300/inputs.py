@@ -1,0 +1,153 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the CPU oracle.
+
+This module holds no arithmetic of the wave method itself (no stencil weights,
+no time stepping, no CFL limit, no wavelet): only velocity models, point
+positions and random traces, drawn from NumPy's PCG64 generator with explicit
+seeds.  Coordinates are x-first per point; model arrays are C-order with the
+axes reversed ((n_z, n_y, n_x) in 3D, (n_z, n_x) in 2D); velocities are km/s
+and the squared slowness is ``1/v**2``.
+"""
+
+import numpy as np
+
+
+def rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def slowness2(v):
+    """Squared slowness m = 1/v^2 (float32) from a velocity array in km/s."""
+    v = np.asarray(v, dtype=np.float64)
+    return (1.0 / (v * v)).astype(np.float32)
+
+
+def _depth_axis(shape_xyz, spacing):
+    nd = len(shape_xyz)
+    nz = shape_xyz[-1]
+    z = np.arange(nz, dtype=np.float64) * spacing[-1]
+    return z.reshape((nz,) + (1,) * (nd - 1))
+
+
+def constant_velocity(shape_xyz, v):
+    return np.full(tuple(shape_xyz)[::-1], float(v), dtype=np.float64)
+
+
+def smooth_gaussian_noise(shape_xyz, corr_len_points, seed):
+    """Unit-variance white noise smoothed by a Gaussian kernel of standard
+    deviation ``corr_len_points`` grid points, renormalised to unit std."""
+    from scipy.ndimage import gaussian_filter
+    g = rng(seed).standard_normal(tuple(shape_xyz)[::-1], dtype=np.float32)
+    g = gaussian_filter(g, sigma=float(corr_len_points), mode="wrap")
+    g -= g.mean(dtype=np.float64)
+    g /= g.std(dtype=np.float64)
+    return g
+
+
+def two_layer_random_velocity(shape_xyz, spacing, v_top=1.5, v_bottom=2.5, interface=None,
+                              sigma=0.05, corr_len=50.0, seed=7):
+    """Two layers split at ``interface`` metres depth (default: mid-depth), times
+    ``1 + sigma * g`` with g smoothed Gaussian noise of correlation length
+    ``corr_len`` metres."""
+    nz = shape_xyz[-1]
+    if interface is None:
+        interface = 0.5 * (nz - 1) * spacing[-1]
+    z = _depth_axis(shape_xyz, spacing)
+    v = np.where(z < interface, v_top, v_bottom) * np.ones(tuple(shape_xyz)[::-1])
+    if sigma:
+        g = smooth_gaussian_noise(shape_xyz, corr_len / spacing[0], seed)
+        v = v * (1.0 + sigma * g)
+    return v
+
+
+def linear_gradient_velocity(shape_xyz, spacing, v0=1.5, k=0.6):
+    """v(z) = v0 + k * z[km]."""
+    z = _depth_axis(shape_xyz, spacing)
+    return (v0 + k * z / 1000.0) * np.ones(tuple(shape_xyz)[::-1])
+
+
+def gaussian_anomalies(shape_xyz, spacing, n=3, amp=0.2, sigma_m=150.0, seed=11):
+    """Sum of ``n`` Gaussian blobs of amplitude +-amp km/s at seeded positions."""
+    r = rng(seed)
+    nd = len(shape_xyz)
+    ext = [(s - 1) * h for s, h in zip(shape_xyz, spacing)]
+    axes = [np.arange(s, dtype=np.float64) * h for s, h in zip(shape_xyz, spacing)]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")[::-1]   # x-first list of arrays
+    out = np.zeros(tuple(shape_xyz)[::-1])
+    for _ in range(n):
+        c = [r.uniform(0.25 * e, 0.75 * e) for e in ext]
+        s = amp if r.uniform() < 0.5 else -amp
+        d2 = sum((grids[d] - c[d]) ** 2 for d in range(nd))
+        out += s * np.exp(-d2 / (2.0 * sigma_m ** 2))
+    return out
+
+
+def layered_velocity(shape_xyz, spacing, n_layers, v_min=1.5, v_max=4.5, perturb=0.05, seed=0):
+    """``n_layers`` flat layers with sorted velocities drawn in [v_min, v_max],
+    interfaces at sorted random depths, each layer scaled by 1 + U(-perturb, perturb)."""
+    r = rng(seed)
+    nz = shape_xyz[-1]
+    depth = (nz - 1) * spacing[-1]
+    vs = np.sort(r.uniform(v_min, v_max, size=n_layers))
+    vs[0] = v_min
+    cuts = np.sort(r.uniform(0.05 * depth, 0.95 * depth, size=n_layers - 1))
+    z = _depth_axis(shape_xyz, spacing)
+    v = np.full(z.shape, vs[0])
+    for i, c in enumerate(cuts):
+        v = np.where(z >= c, vs[i + 1], v)
+    v = v * (1.0 + r.uniform(-perturb, perturb, size=v.shape))
+    v = np.clip(v, v_min, v_max)
+    return v * np.ones(tuple(shape_xyz)[::-1])
+
+
+def salt_body(v, shape_xyz, spacing, semi_axes_m=(1500.0, 1000.0, 600.0), v_salt=4.5, seed=5):
+    """Overwrite an ellipsoid (centred mid-model, jittered by seed) with v_salt."""
+    r = rng(seed)
+    nd = len(shape_xyz)
+    ext = [(s - 1) * h for s, h in zip(shape_xyz, spacing)]
+    c = [0.5 * e + r.uniform(-0.05, 0.05) * e for e in ext]
+    axes = [np.arange(s, dtype=np.float64) * h for s, h in zip(shape_xyz, spacing)]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")[::-1]
+    q = sum(((grids[d] - c[d]) / semi_axes_m[d]) ** 2 for d in range(nd))
+    out = np.array(v, copy=True)
+    out[q <= 1.0] = v_salt
+    return out
+
+
+def line_receivers_jittered(n, x0, dx, depth, h, extent_xz, seed=1234):
+    """2D receivers: x_i = x0 + i*dx at ``depth``; each coordinate jittered by
+    U[-h/2, h/2) and clamped inside [0, extent]."""
+    r = rng(seed)
+    x = x0 + dx * np.arange(n, dtype=np.float64)
+    z = np.full(n, float(depth))
+    x = x + r.uniform(-0.5 * h, 0.5 * h, size=n)
+    z = z + r.uniform(-0.5 * h, 0.5 * h, size=n)
+    x = np.clip(x, 0.0, extent_xz[0])
+    z = np.clip(z, 0.0, extent_xz[1])
+    return np.stack([x, z], axis=1).astype(np.float32)
+
+
+def surface_grid_receivers(nx, ny, spacing_xy, depth, origin_xy=(0.0, 0.0)):
+    """3D receivers on an nx-by-ny grid at constant depth (x fastest)."""
+    x = origin_xy[0] + spacing_xy[0] * np.arange(nx, dtype=np.float64)
+    y = origin_xy[1] + spacing_xy[1] * np.arange(ny, dtype=np.float64)
+    X, Y = np.meshgrid(x, y, indexing="xy")
+    Z = np.full(X.shape, float(depth))
+    return np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1).astype(np.float32)
+
+
+def random_points(n, shape_xyz, spacing, seed, margin=0.0):
+    """Uniform random off-grid points inside the physical domain."""
+    r = rng(seed)
+    ext = [(s - 1) * h for s, h in zip(shape_xyz, spacing)]
+    cols = [r.uniform(margin, e - margin, size=n) for e in ext]
+    return np.stack(cols, axis=1).astype(np.float32)
+
+
+def random_traces(nt, n, seed, scale=1.0):
+    return (scale * rng(seed).standard_normal((nt, n))).astype(np.float32)
+
+
+def smooth_perturbation(shape_xyz, spacing, seed, corr_len=30.0):
+    """A smooth, bounded model perturbation (unit max-abs) for Taylor tests."""
+    g = smooth_gaussian_noise(shape_xyz, corr_len / spacing[0], seed).astype(np.float64)
+    return g / np.abs(g).max()
