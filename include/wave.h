@@ -1,0 +1,241 @@
+/*
+ * wave.h -- C ABI of the GB300 (sm_103a) damped acoustic wave library.
+ *
+ * The library implements the hot path of Kukreja et al., "Devito: automated
+ * fast finite difference computation" (arXiv 1608.08658):
+ *
+ *   * the forward leapfrog solve of  m u_tt - lap(u) + eta u_t = q
+ *     (Eq. 1 with the damping term of Listing 1), with receiver sampling,
+ *   * its exact discrete adjoint (Listing 2, Eq. 4),
+ *   * the adjoint-state FWI gradient of the objective of Eq. 2 (Eq. 3).
+ *
+ * Discretisation (shared with the FP64 oracle by specification only):
+ *   a u^{k+1} - b u^k + c u^{k-1} = P_s^T q^k,   k = 0 .. nt-2,
+ *   a = m/dt^2 + eta/(2dt),  b = 2m/dt^2 + L,  c = m/dt^2 - eta/(2dt),
+ *   u^{-1} = u^0 = 0,   d^n = P_r u^n for n = 0 .. nt-1,
+ * where L is the centred Laplacian of even space order 2..16 (Sec. IV-A1)
+ * with zero values outside the computational grid, eta is a quadratic sponge
+ * in the nbl absorbing points added on every side (Sec. V-D), and P_s / P_r
+ * are multilinear (bi/tri-linear) sparse-point interpolation operators (Sec. IV).
+ *
+ * Conventions common to every entry point
+ * ---------------------------------------
+ * Axes:   axis 0 is x (fastest in memory); axis 1 is y in 3D or depth z in 2D;
+ *         axis 2 is depth z in 3D.  A physical field is a dense C-order array
+ *         [N_z][N_y][N_x] (3D) or [N_z][N_x] (2D) of float32.
+ * Units:  spacing in m, time in ms, velocity in km/s, squared slowness
+ *         m = 1/v^2 in s^2/km^2; frequencies in kHz.
+ * Memory: every array argument may be a device pointer (CUDA global memory on
+ *         the context's device) or a host pointer (pageable or pinned); the
+ *         library detects which and stages host arrays through its own
+ *         workspace.  The caller owns all argument buffers; the context owns
+ *         its workspace (wavefields, coefficients, snapshots, checkpoints).
+ * Streams: work is enqueued on the CUDA stream passed as `stream`
+ *         (cudaStream_t cast to void*, NULL = legacy default stream).  Every
+ *         compute entry point returns after that stream has completed the
+ *         call's work, so outputs are ready on return.
+ * Errors: every call returns an int status, 0 on success (the generated
+ *         operator of Listing 3 also returns 0).  Failures never abort the
+ *         process and never throw across the ABI; wave_last_error() gives a
+ *         one-line description.  A call that fails leaves its outputs
+ *         unspecified.
+ * Threads: a context may be used by one host thread at a time.
+ */
+#ifndef WAVE_H_
+#define WAVE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define WAVE_API __attribute__((visibility("default")))
+#else
+#define WAVE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define WAVE_OK                 0
+#define WAVE_ERR_INVALID_ARG    1  /* null pointer, bad size, bad space order, ... */
+#define WAVE_ERR_POINT_OUTSIDE  2  /* a source/receiver lies outside the physical domain */
+#define WAVE_ERR_UNSTABLE_DT    3  /* dt above the leapfrog stability limit */
+#define WAVE_ERR_OUT_OF_MEMORY  4  /* workspace would exceed the budget, or cudaMalloc failed */
+#define WAVE_ERR_CUDA           5  /* a CUDA runtime/driver call or kernel launch failed */
+#define WAVE_ERR_TIMEOUT        6  /* a bounded device-side wait expired (kernel gave up) */
+#define WAVE_ERR_NOT_SUPPORTED  7  /* feature/size not supported by this build or device */
+
+typedef struct wave_context wave_context;
+
+/* Physical grid plus absorbing layer (Sec. V-D: the layer is added outside the
+ * model on every side, so the computational grid has N_d + 2*nbl points per
+ * axis and its node 0 sits at origin_d - nbl*spacing_d).
+ * sponge_vref (km/s) sets the sponge strength
+ *   eta(i) = sum_d eta_max_d (delta_d(i)/nbl)^2,
+ *   eta_max_d = 3 * sponge_vref * ln(1000) / (2 * nbl * spacing_d),
+ * with delta_d the number of points into the layer (1..nbl); it is a fixed
+ * parameter (not derived from m) so that eta does not depend on the model. */
+typedef struct {
+  int32_t ndim;          /* 2 or 3 */
+  int32_t nbl;           /* absorbing points per side, >= 0 */
+  int64_t shape[3];      /* physical points per axis, x-first; shape[2] ignored in 2D */
+  double spacing[3];     /* grid spacing per axis, m, > 0 */
+  double origin[3];      /* coordinate of physical node 0 per axis, m */
+  double sponge_vref;    /* km/s, > 0 when nbl > 0 */
+} wave_geometry;
+
+/* A set of off-grid points (sources or receivers): n points, `coords` holds
+ * n*ndim float32 values, x-first per point, physical coordinates in m (host
+ * or device pointer).  Interpolation (Sec. IV, sparse-point interpolation):
+ * per axis t = (p - o)/h on the computational grid, i = floor(t), f = t - i,
+ * (i = n-2, f = 1 on the last node); corner weights are products of (1-f, f).
+ * Every point must lie inside the physical domain (WAVE_ERR_POINT_OUTSIDE). */
+typedef struct {
+  int64_t n;
+  const float* coords;
+} wave_points;
+
+/* Storage of the forward wavefield for the imaging condition of Eq. 3.
+ * FULL_*: every time level u^1..u^{nt-1} is kept (Sec. IV-B4 "save" flag).
+ * CHECKPOINT_*: only exact FP32 checkpoints (u^{k-1}, u^k) every S steps are
+ * kept; each segment is recomputed before its adjoint sweep.
+ * *_BF16 / *_FP16: snapshots are stored in 16 bits with one power-of-two
+ * scale per slab of 64 (x) by 2 (axis 1) points of one plane; all stencil
+ * arithmetic and gradient accumulation stay FP32.
+ * AUTO: FULL_FP32 if it fits the budget, else CHECKPOINT_FP32. */
+typedef enum {
+  WAVE_SNAP_FULL_FP32 = 0,
+  WAVE_SNAP_FULL_BF16 = 1,
+  WAVE_SNAP_FULL_FP16 = 2,
+  WAVE_SNAP_CHECKPOINT_FP32 = 3,
+  WAVE_SNAP_CHECKPOINT_BF16 = 4,
+  WAVE_SNAP_CHECKPOINT_FP16 = 5,
+  WAVE_SNAP_AUTO = 6
+} wave_snap_mode;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the
+ * workspace the context may hold (0 = no cap beyond free device memory).
+ * Workspace is allocated lazily by the compute calls and reused across calls.
+ * Errors: INVALID_ARG (ctx NULL), CUDA (no device / sm_103a kernels cannot run). */
+WAVE_API int wave_context_create(wave_context** ctx, int device, size_t hbm_budget_bytes);
+
+/* Release the context and all its workspace.  NULL is accepted. */
+WAVE_API int wave_context_destroy(wave_context* ctx);
+
+/* Bytes of device workspace currently held by the context. */
+WAVE_API size_t wave_context_workspace_bytes(const wave_context* ctx);
+
+/* Release all workspace (the next call re-allocates what it needs). */
+WAVE_API int wave_context_trim(wave_context* ctx);
+
+/* Checkpoint interval S (steps) for CHECKPOINT_* modes; 0 = choose from the
+ * budget (default). */
+WAVE_API int wave_context_set_checkpoint_interval(wave_context* ctx, int steps);
+
+/* Text of a status code, and the last error message of a context. */
+WAVE_API const char* wave_error_string(int status);
+WAVE_API const char* wave_last_error(const wave_context* ctx);
+
+/* ---- method -------------------------------------------------------------- */
+
+/* Forward modelling (Listing 1; Eq. 1 with damping).
+ * m:     physical squared slowness, dense [N_z][N_y][N_x] (2D: [N_z][N_x]).
+ * src:   n_s source points; q: source traces [nt][n_s] (row k enters the
+ *        update of time row k, producing u^{k+1}; row nt-1 is unused).
+ * rec:   n_r receiver points; d_out: receiver data [nt][n_r], d^n = P_r u^n.
+ * dt:    time step (ms), must not exceed wave_dt_max() for v_max = 1/sqrt(min m).
+ * nt:    number of time levels (>= 2); space_order: even, 2..16.
+ * Errors: INVALID_ARG, POINT_OUTSIDE, UNSTABLE_DT, OUT_OF_MEMORY, CUDA, TIMEOUT. */
+WAVE_API int wave_forward(wave_context* ctx, const wave_geometry* geom, const float* m,
+                 const wave_points* src, const float* q, const wave_points* rec,
+                 float* d_out, float dt, int nt, int space_order, void* stream);
+
+/* Same as wave_forward with optional initial and final states on the
+ * computational grid (dense [n_z][n_y][n_x] float32, n_d = N_d + 2 nbl):
+ * u_init_prev = u^{-1}, u_init = u^0 (NULL = zero, the initial condition of
+ * Eq. 1); u_final_prev = u^{nt-2}, u_final = u^{nt-1} are written when not
+ * NULL.  Used to check single steps of the stencil against the oracle. */
+WAVE_API int wave_forward_ex(wave_context* ctx, const wave_geometry* geom, const float* m,
+                    const wave_points* src, const float* q, const wave_points* rec,
+                    float* d_out, float dt, int nt, int space_order,
+                    const float* u_init_prev, const float* u_init,
+                    float* u_final_prev, float* u_final, void* stream);
+
+/* Adjoint modelling (Listing 2 read as the exact transpose of wave_forward;
+ * Eq. 4 with P_r^* applied to receiver-side traces).
+ * y:     receiver-side traces [nt][n_r] (row 0 has no effect: u^0 is fixed);
+ * q_out: source-side traces [nt][n_s] = F^T y; row nt-1 is zero.
+ * Recursion: lam_{j-1} = (b lam_j - c lam_{j+1} + P_r^T y^j)/a, j = nt-1..1,
+ * lam_{nt-1} = lam_nt = 0, q_out^k = P_s lam_k.
+ * Errors: as wave_forward. */
+WAVE_API int wave_adjoint(wave_context* ctx, const wave_geometry* geom, const float* m,
+                 const wave_points* src, const wave_points* rec, const float* y,
+                 float* q_out, float dt, int nt, int space_order, void* stream);
+
+/* FWI gradient by the adjoint-state method (Eq. 2-4).
+ * Runs the forward model, forms the residual r = P_r u - d_obs [nt][n_r], the
+ * objective phi = 0.5 sum r^2 (accumulated in FP64) and the gradient
+ *   g = -(1/dt^2) sum_{j=1}^{nt-1} u^j (lam_{j-1} - 2 lam_j + lam_{j+1})
+ * with lam the adjoint field for y = r, folded onto the physical grid by the
+ * transpose of the edge-replicating padding.
+ * grad_out: physical grid, same layout as m.  phi_out: host double (may be NULL).
+ * resid_out: optional [nt][n_r] residual (NULL = not returned).
+ * snap_mode: a wave_snap_mode value.
+ * Errors: as wave_forward; OUT_OF_MEMORY when the chosen storage cannot fit. */
+WAVE_API int wave_gradient(wave_context* ctx, const wave_geometry* geom, const float* m,
+                  const wave_points* src, const float* q, const wave_points* rec,
+                  const float* d_obs, float* grad_out, double* phi_out, float* resid_out,
+                  int snap_mode, float dt, int nt, int space_order, void* stream);
+
+/* Gradient back-propagation for a given receiver-side adjoint source: same as
+ * wave_gradient but with the residual replaced by `y` [nt][n_r] (so that
+ * grad_out = J^T y, the vector-Jacobian product of the map m -> d used by an
+ * autograd backward pass).  d_out, if not NULL, receives the forward data. */
+WAVE_API int wave_jacobian_adjoint(wave_context* ctx, const wave_geometry* geom, const float* m,
+                          const wave_points* src, const float* q, const wave_points* rec,
+                          const float* y, float* grad_out, float* d_out,
+                          int snap_mode, float dt, int nt, int space_order, void* stream);
+
+/* ---- helpers (host-side, no device work) ---------------------------------- */
+
+/* Centred second-derivative weights [w_0, w_1, .., w_R], R = space_order/2
+ * (Sec. IV-A1; closed form w_0 = -2 sum 1/j^2,
+ * w_j = 2 (-1)^{j+1} (R!)^2 / (j^2 (R-j)! (R+j)!)).  w_out holds R+1 doubles. */
+WAVE_API int wave_fd_weights(int space_order, double* w_out);
+
+/* Leapfrog stability limit dt_max = 2 / (v_max sqrt(sum_d (sum_j |w_j|)/h_d^2))
+ * for the undamped scheme; returns a negative value on invalid input. */
+WAVE_API double wave_dt_max(int ndim, const double* spacing, int space_order, double v_max);
+
+/* Ricker wavelet r(t_n) = (1 - 2 (pi f0 (t_n - t0))^2) exp(-(pi f0 (t_n - t0))^2),
+ * t_n = n dt, n = 0..nt-1 (Sec. V-D source); q_out: nt float32 (host or device). */
+WAVE_API int wave_ricker(float* q_out, int nt, float dt, float f0, float t0);
+
+/* ---- instrumentation --------------------------------------------------- */
+
+/* Kernel kinds for wave_context_kernel_stats. */
+#define WAVE_KERNEL_STEP        0  /* stencil step (forward/adjoint, any epilogue) */
+#define WAVE_KERNEL_STEP_SNAP   1  /* stencil step storing a snapshot */
+#define WAVE_KERNEL_STEP_GRAD   2  /* adjoint step with the imaging condition */
+#define WAVE_KERNEL_SPARSE      3  /* source injection / receiver sampling */
+#define WAVE_KERNEL_OTHER       4  /* set-up, residual, fold, snapshot store, copies */
+#define WAVE_KERNEL_KINDS       5
+
+/* Enable (1) or disable (0) per-launch CUDA-event timing of the context's
+ * kernels on the stream they are launched on.  Disabled by default. */
+WAVE_API int wave_context_set_profiling(wave_context* ctx, int enable);
+
+/* Launch count (always counted) and summed event time in ms (when profiling)
+ * of one kernel kind since the last reset; totals over all kinds when
+ * kind < 0. */
+WAVE_API int wave_context_kernel_stats(wave_context* ctx, int kind, int64_t* launches, double* total_ms);
+WAVE_API int wave_context_reset_stats(wave_context* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WAVE_H_ */

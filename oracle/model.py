@@ -81,12 +81,18 @@ class Geometry:
         return self.shape[::-1]
 
 
-def pad_model(geom, m_phys):
-    """Extend the physical model by ``nbl`` points on every side by edge replication."""
-    m_phys = np.asarray(m_phys, dtype=np.float64)
+def pad_model(geom, m_phys, window=None):
+    """Extend the physical model by ``nbl`` points on every side by edge replication.
+
+    ``window`` (optional): per array axis ``(start, stop)`` on the computational
+    grid; only that block of the padded model is formed (same values)."""
+    m_phys = np.asarray(m_phys)
     if m_phys.shape != geom.phys_array_shape:
         raise ValueError("model shape %r != %r" % (m_phys.shape, geom.phys_array_shape))
-    return np.pad(m_phys, geom.nbl, mode="edge")
+    if window is None:
+        return np.pad(m_phys.astype(np.float64), geom.nbl, mode="edge")
+    idx = [np.clip(np.arange(a, b) - geom.nbl, 0, n - 1) for (a, b), n in zip(window, m_phys.shape)]
+    return m_phys[np.ix_(*idx)].astype(np.float64)
 
 
 def fold_gradient(geom, g_comp):
@@ -122,18 +128,23 @@ def sponge_depth(n, nbl):
     return d
 
 
-def damping(geom):
-    """Sponge damping eta (1/ms) on the computational grid, array layout."""
+def damping(geom, window=None):
+    """Sponge damping eta (1/ms) on the computational grid, array layout
+    (optionally only the block ``window``, per array axis ``(start, stop)``)."""
     nd = geom.ndim
-    eta = np.zeros(geom.array_shape, dtype=np.float64)
+    if window is None:
+        window = [(0, n) for n in geom.array_shape]
+    eta = np.zeros(tuple(b - a for a, b in window), dtype=np.float64)
     if geom.nbl == 0:
         return eta
     for d in range(nd):
+        ax = nd - 1 - d
         n = geom.comp_shape[d]
         eta_max = 3.0 * geom.sponge_vref * log(1.0 / REFLECTION_COEFF) / (2.0 * geom.nbl * geom.spacing[d])
-        prof = eta_max * (sponge_depth(n, geom.nbl) / geom.nbl) ** 2
+        a, b = window[ax]
+        prof = eta_max * (sponge_depth(n, geom.nbl)[a:b] / geom.nbl) ** 2
         shape = [1] * nd
-        shape[nd - 1 - d] = n
+        shape[ax] = b - a
         eta = eta + prof.reshape(shape)
     return eta
 

@@ -1,0 +1,57 @@
+// Runtime dispatch of the stencil step over the stencil radius.
+#include "step_kernel.cuh"
+
+namespace wave {
+
+#define WAVE_DECLARE_RADIUS(RR)                                                                          \
+  cudaError_t launch_step_r##RR(int ndim, int mode, const StepMaps& maps, const StepParams& p, dim3 grid, \
+                                cudaStream_t s);                                                        \
+  int step_smem_r##RR(int ndim, int mode);
+WAVE_DECLARE_RADIUS(1)
+WAVE_DECLARE_RADIUS(2)
+WAVE_DECLARE_RADIUS(3)
+WAVE_DECLARE_RADIUS(4)
+WAVE_DECLARE_RADIUS(5)
+WAVE_DECLARE_RADIUS(6)
+WAVE_DECLARE_RADIUS(7)
+WAVE_DECLARE_RADIUS(8)
+
+cudaError_t launch_step(int R, int ndim, int mode, const StepMaps& maps, const StepParams& p, dim3 grid,
+                        cudaStream_t stream) {
+  switch (R) {
+    case 1: return launch_step_r1(ndim, mode, maps, p, grid, stream);
+    case 2: return launch_step_r2(ndim, mode, maps, p, grid, stream);
+    case 3: return launch_step_r3(ndim, mode, maps, p, grid, stream);
+    case 4: return launch_step_r4(ndim, mode, maps, p, grid, stream);
+    case 5: return launch_step_r5(ndim, mode, maps, p, grid, stream);
+    case 6: return launch_step_r6(ndim, mode, maps, p, grid, stream);
+    case 7: return launch_step_r7(ndim, mode, maps, p, grid, stream);
+    case 8: return launch_step_r8(ndim, mode, maps, p, grid, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int step_smem_bytes(int R, int ndim, int mode) {
+  switch (R) {
+    case 1: return step_smem_r1(ndim, mode);
+    case 2: return step_smem_r2(ndim, mode);
+    case 3: return step_smem_r3(ndim, mode);
+    case 4: return step_smem_r4(ndim, mode);
+    case 5: return step_smem_r5(ndim, mode);
+    case 6: return step_smem_r6(ndim, mode);
+    case 7: return step_smem_r7(ndim, mode);
+    case 8: return step_smem_r8(ndim, mode);
+    default: return -1;
+  }
+}
+
+int step_threads() { return StepTraits<1, 3>::NTHREADS; }
+int step_bx() { return StepTraits<1, 3>::BX; }
+int step_by(int R, int ndim) {
+  (void)R;
+  (void)ndim;
+  return StepTraits<1, 3>::BY;
+}
+int step_hx(int R) { return R <= 4 ? 4 : 8; }
+
+}  // namespace wave

@@ -1,0 +1,398 @@
+// One leapfrog time level of the damped acoustic operator (Listing 1 / Eq. 1),
+// which is also one level of its adjoint (Listing 2): with
+//   a = m/dt^2 + eta/(2dt), b = 2m/dt^2 + L, c = m/dt^2 - eta/(2dt)
+// the new level is (b*cur - c*prev)/a; dividing by m/dt^2 and writing
+// cm = dt^2/m, k = eta*cm/(2dt):
+//   new = (2*cur - (1-k)*prev + cm*L(cur)) / (1+k).
+// The adjoint recursion lam_{j-1} = (b lam_j - c lam_{j+1} + ...)/a has the
+// same form, so one kernel serves both; the epilogue variant adds a snapshot
+// store (forward with storage for Eq. 3) or the imaging condition of Eq. 3
+//   g -= u^j * (lam_{j-1} - 2 lam_j + lam_{j+1}) / dt^2 .
+//
+// Data movement (3D): a CTA owns a BX x BY column tile and streams a chunk of
+// planes along axis 2.  A producer warp issues TMA tile loads: each plane of
+// the centre level with its x/y halo into a ring of NSU stages, and the
+// per-point tiles (previous level, cm, and for the gradient g and the
+// snapshot) into a ring of NSP stages; mbarriers carry the transaction
+// counts.  Eight consumer warps keep the 2R+1 centre-level values of their
+// columns in a register queue (the z taps), read x/y taps from the centre
+// plane in shared memory, and write the new level with 16-byte stores.
+// Zero ghost values outside the grid come from the TMA out-of-bounds fill.
+// Every barrier wait is bounded; on expiry the kernel records a timeout in the
+// status word, drains its own copies and returns.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "ptx.cuh"
+#include "wave_internal.h"
+
+namespace wave {
+namespace dev {
+
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+__device__ __forceinline__ void fma4(float4& acc, float c, const float4& a, const float4& b) {
+  acc.x = fmaf(c, a.x + b.x, acc.x);
+  acc.y = fmaf(c, a.y + b.y, acc.y);
+  acc.z = fmaf(c, a.z + b.z, acc.z);
+  acc.w = fmaf(c, a.w + b.w, acc.w);
+}
+
+__device__ __forceinline__ float get(const float4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+__device__ __forceinline__ float damp_inv(float eta, float cm, float half_inv_dt, float& one_minus_k) {
+  const float k = eta * cm * half_inv_dt;
+  one_minus_k = 1.f - k;
+  return eta == 0.f ? 1.f : __frcp_rn(1.f + k);
+}
+
+template <int FMT>
+__device__ __forceinline__ void store_snap4(void* base, long long idx, const float4& v, float inv_s) {
+  if (FMT == 0) {
+    *reinterpret_cast<float4*>(static_cast<float*>(base) + idx) = v;
+  } else if (FMT == 1) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(v.x * inv_s, v.y * inv_s);
+    __nv_bfloat162 b = __floats2bfloat162_rn(v.z * inv_s, v.w * inv_s);
+    uint2 u;
+    u.x = *reinterpret_cast<uint32_t*>(&a);
+    u.y = *reinterpret_cast<uint32_t*>(&b);
+    *reinterpret_cast<uint2*>(static_cast<uint16_t*>(base) + idx) = u;
+  } else {
+    __half2 a = __floats2half2_rn(v.x * inv_s, v.y * inv_s);
+    __half2 b = __floats2half2_rn(v.z * inv_s, v.w * inv_s);
+    uint2 u;
+    u.x = *reinterpret_cast<uint32_t*>(&a);
+    u.y = *reinterpret_cast<uint32_t*>(&b);
+    *reinterpret_cast<uint2*>(static_cast<uint16_t*>(base) + idx) = u;
+  }
+}
+
+template <int FMT>
+__device__ __forceinline__ float4 load_snap4_smem(const unsigned char* p, float s) {
+  if (FMT == 0) return *reinterpret_cast<const float4*>(p);
+  const uint2 u = *reinterpret_cast<const uint2*>(p);
+  float2 a, b;
+  if (FMT == 1) {
+    a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+    b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+  } else {
+    a = __half22float2(*reinterpret_cast<const __half2*>(&u.x));
+    b = __half22float2(*reinterpret_cast<const __half2*>(&u.y));
+  }
+  return make_float4(a.x * s, a.y * s, b.x * s, b.y * s);
+}
+
+template <int R, int NDIM, int MODE>
+__global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS)
+    step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
+                const __grid_constant__ CUtensorMap tm_cm, const __grid_constant__ CUtensorMap tm_g,
+                const __grid_constant__ CUtensorMap tm_s, const StepParams p) {
+  using T = StepTraits<R, NDIM>;
+  using L = StepLayout<R, NDIM, MODE>;
+  constexpr int RZ = T::RZ;
+  constexpr int FMT = mode_snap_fmt(MODE);
+
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+  uint64_t* fullU = reinterpret_cast<uint64_t*>(smem);
+  uint64_t* emptyU = fullU + T::NSU;
+  uint64_t* fullP = emptyU + T::NSU;
+  uint64_t* emptyP = fullP + T::NSP;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(emptyP + T::NSP);
+  float* Ubase = reinterpret_cast<float*>(smem + L::U_OFF);
+  unsigned char* Pbase = smem + L::PST_OFF;
+
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5;
+  const int lane = tid & 31;
+  const int x0 = blockIdx.x * T::BX;
+  const int y0 = blockIdx.y * T::BY;
+  const int z0 = blockIdx.z * p.zchunk;
+  const int z1 = min(z0 + p.zchunk, p.NZ);
+  const int nP = z1 - z0;
+  const int nU = nP + 2 * RZ;
+  if (nP <= 0) return;
+
+  if (tid == 0) {
+    for (int i = 0; i < T::NSU; ++i) {
+      mbar_init(&fullU[i], 1);
+      mbar_init(&emptyU[i], T::NCW);
+    }
+    for (int i = 0; i < T::NSP; ++i) {
+      mbar_init(&fullP[i], 1);
+      mbar_init(&emptyP[i], T::NCW);
+    }
+    *abort_flag = 0;
+    fence_mbarrier_init();
+  }
+  __syncthreads();
+
+  // ------------------------------------------------------------------ producer
+  if (warp == T::NCW) {
+    if (lane == 0) {
+      prefetch_tensormap(&tm_u);
+      prefetch_tensormap(&tm_p);
+      prefetch_tensormap(&tm_cm);
+      if (mode_is_grad(MODE)) {
+        prefetch_tensormap(&tm_g);
+        prefetch_tensormap(&tm_s);
+      }
+      int issuedU = 0, issuedP = 0;
+      bool ok = true;
+      for (int s = 0; s < nU; ++s) {
+        const int slot = s % T::NSU;
+        if (s >= T::NSU) ok = mbar_wait_bounded(&emptyU[slot], ((s / T::NSU) - 1) & 1, abort_flag, kWaitLimitNs);
+        if (!ok) break;
+        mbar_arrive_expect_tx(&fullU[slot], T::U_BYTES);
+        tma_load_4d(Ubase + slot * (T::U_STRIDE / 4), &tm_u, x0 - T::HX, y0 - R, z0 - RZ + s, p.cur, &fullU[slot]);
+        issuedU = s + 1;
+        if (s >= 2 * RZ) {
+          const int j = s - 2 * RZ;
+          const int ps = j % T::NSP;
+          if (j >= T::NSP) ok = mbar_wait_bounded(&emptyP[ps], ((j / T::NSP) - 1) & 1, abort_flag, kWaitLimitNs);
+          if (!ok) break;
+          unsigned char* pd = Pbase + ps * L::P_BYTES;
+          mbar_arrive_expect_tx(&fullP[ps], L::P_BYTES);
+          tma_load_4d(pd + L::PREV_OFF, &tm_p, x0, y0, z0 + j, p.prev, &fullP[ps]);
+          tma_load_3d(pd + L::CM_OFF, &tm_cm, x0, y0, z0 + j, &fullP[ps]);
+          if (mode_is_grad(MODE)) {
+            tma_load_3d(pd + L::G_OFF, &tm_g, x0, y0, z0 + j, &fullP[ps]);
+            tma_load_4d(pd + L::S_OFF, &tm_s, x0, y0, z0 + j, p.snap_level, &fullP[ps]);
+          }
+          issuedP = j + 1;
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicExch(p.status, kDevTimeout);
+      }
+      if (*abort_flag) {
+        // let every copy this thread issued land before the CTA exits
+        for (int slot = 0; slot < T::NSU; ++slot) {
+          if (issuedU > slot) {
+            const int last = slot + T::NSU * ((issuedU - 1 - slot) / T::NSU);
+            mbar_wait_bounded(&fullU[slot], (last / T::NSU) & 1, nullptr, kWaitLimitNs);
+          }
+        }
+        for (int slot = 0; slot < T::NSP; ++slot) {
+          if (issuedP > slot) {
+            const int last = slot + T::NSP * ((issuedP - 1 - slot) / T::NSP);
+            mbar_wait_bounded(&fullP[slot], (last / T::NSP) & 1, nullptr, kWaitLimitNs);
+          }
+        }
+      }
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------------ consumers
+  const int ty = tid >> 4;  // row of the tile, 0..15
+  const int tx = tid & 15;  // quad of 4 x points
+  const int gx = x0 + 4 * tx;
+  const int gy = y0 + ty;
+  const bool store_ok = (gx < p.NX) && (gy < p.NY);
+  const int lofs = (R + ty) * T::UW + T::HX + 4 * tx;  // centre of this quad in a U stage
+
+  // sponge along x (per point) and axis 1 (per row)
+  float ex[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) ex[i] = sponge_term(gx + i, p.NX, p.nblx, p.emx);
+  const float ey = sponge_term(gy, p.NY, p.nbly, p.emy);
+
+  float4 q[2 * RZ + 1];
+#pragma unroll
+  for (int i = 0; i < 2 * RZ + 1; ++i) q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+
+  bool ok = true;
+#pragma unroll
+  for (int s = 0; s < 2 * RZ; ++s) {
+    const int slot = s % T::NSU;
+    ok = mbar_wait_bounded(&fullU[slot], (s / T::NSU) & 1, abort_flag, kWaitLimitNs);
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok) break;
+    q[s + 1] = lds4(Ubase + slot * (T::U_STRIDE / 4) + lofs);
+    if (s < RZ) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&emptyU[slot]);
+    }
+  }
+
+  const long long plane_elems = static_cast<long long>(p.NY) * p.pitch;
+  for (int j = 0; j < nP && ok; ++j) {
+    const int sn = j + 2 * RZ;  // sequence number of plane z+R
+    const int sc = j + RZ;      // sequence number of the centre plane z
+    const int un = sn % T::NSU;
+    const int uc = sc % T::NSU;
+    ok = mbar_wait_bounded(&fullU[un], (sn / T::NSU) & 1, abort_flag, kWaitLimitNs);
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok) break;
+#pragma unroll
+    for (int i = 0; i < 2 * RZ; ++i) q[i] = q[i + 1];
+    q[2 * RZ] = lds4(Ubase + un * (T::U_STRIDE / 4) + lofs);
+    const float4 c = q[RZ];
+    const float* Uc = Ubase + uc * (T::U_STRIDE / 4) + lofs;
+
+    // Laplacian: centre, streamed axis from registers, axis 1 and x from smem
+    float4 lap = make_float4(p.c0 * c.x, p.c0 * c.y, p.c0 * c.z, p.c0 * c.w);
+#pragma unroll
+    for (int k = 1; k <= RZ; ++k) fma4(lap, p.cz[k - 1], q[RZ - k], q[RZ + k]);
+#pragma unroll
+    for (int k = 1; k <= R; ++k) fma4(lap, p.cy[k - 1], lds4(Uc - k * T::UW), lds4(Uc + k * T::UW));
+    {
+      constexpr int NQ = T::HX / 4;  // halo quads per side
+      float v[4 + 2 * T::HX];
+#pragma unroll
+      for (int k = 0; k < NQ; ++k) {
+        const float4 l = lds4(Uc - 4 * (k + 1));
+        const float4 r = lds4(Uc + 4 * (k + 1));
+        v[T::HX - 4 * (k + 1) + 0] = l.x;
+        v[T::HX - 4 * (k + 1) + 1] = l.y;
+        v[T::HX - 4 * (k + 1) + 2] = l.z;
+        v[T::HX - 4 * (k + 1) + 3] = l.w;
+        v[T::HX + 4 * (k + 1) + 0] = r.x;
+        v[T::HX + 4 * (k + 1) + 1] = r.y;
+        v[T::HX + 4 * (k + 1) + 2] = r.z;
+        v[T::HX + 4 * (k + 1) + 3] = r.w;
+      }
+      v[T::HX + 0] = c.x;
+      v[T::HX + 1] = c.y;
+      v[T::HX + 2] = c.z;
+      v[T::HX + 3] = c.w;
+#pragma unroll
+      for (int k = 1; k <= R; ++k) {
+        lap.x = fmaf(p.cx[k - 1], v[T::HX + 0 - k] + v[T::HX + 0 + k], lap.x);
+        lap.y = fmaf(p.cx[k - 1], v[T::HX + 1 - k] + v[T::HX + 1 + k], lap.y);
+        lap.z = fmaf(p.cx[k - 1], v[T::HX + 2 - k] + v[T::HX + 2 + k], lap.z);
+        lap.w = fmaf(p.cx[k - 1], v[T::HX + 3 - k] + v[T::HX + 3 + k], lap.w);
+      }
+    }
+
+    const int ps = j % T::NSP;
+    ok = mbar_wait_bounded(&fullP[ps], (j / T::NSP) & 1, abort_flag, kWaitLimitNs);
+    ok = __all_sync(0xffffffffu, ok);
+    if (!ok) break;
+    const unsigned char* Pst = Pbase + ps * L::P_BYTES;
+    const int tofs = (ty * T::BX + 4 * tx) * 4;  // byte offset of this quad in a tile
+    const float4 prev = *reinterpret_cast<const float4*>(Pst + L::PREV_OFF + tofs);
+    const float4 cm = *reinterpret_cast<const float4*>(Pst + L::CM_OFF + tofs);
+
+    const int gz = z0 + j;
+    const float eyz = ey + (NDIM == 3 ? sponge_term(gz, p.NZ, p.nblz, p.emz) : 0.f);
+    float4 out;
+    {
+      float omk;
+      float inv = damp_inv(ex[0] + eyz, cm.x, p.half_inv_dt, omk);
+      out.x = (2.f * c.x - omk * prev.x + cm.x * lap.x) * inv;
+      inv = damp_inv(ex[1] + eyz, cm.y, p.half_inv_dt, omk);
+      out.y = (2.f * c.y - omk * prev.y + cm.y * lap.y) * inv;
+      inv = damp_inv(ex[2] + eyz, cm.z, p.half_inv_dt, omk);
+      out.z = (2.f * c.z - omk * prev.z + cm.z * lap.z) * inv;
+      inv = damp_inv(ex[3] + eyz, cm.w, p.half_inv_dt, omk);
+      out.w = (2.f * c.w - omk * prev.w + cm.w * lap.w) * inv;
+    }
+
+    const long long idx = gz * plane_elems + static_cast<long long>(gy) * p.pitch + gx;
+    if (store_ok) *reinterpret_cast<float4*>(p.fields + p.prev * p.slot_elems + idx) = out;
+
+    if constexpr (mode_is_snap(MODE)) {
+      if constexpr (FMT == 0) {
+        if (store_ok) store_snap4<0>(p.snap_out, idx, c, 1.f);
+      } else {
+        float amax = fmaxf(fmaxf(fabsf(c.x), fabsf(c.y)), fmaxf(fabsf(c.z), fabsf(c.w)));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+        const float s = slab_scale(amax);
+        if (store_ok) store_snap4<FMT>(p.snap_out, idx, c, slab_inv_scale(s));
+        if (lane == 0 && gy < p.NY)
+          p.scale_out[(static_cast<long long>(gz) * p.slabs_y + (gy >> 1)) * p.slabs_x + blockIdx.x] = s;
+      }
+    }
+    if constexpr (mode_is_grad(MODE)) {
+      float s = 1.f;
+      if constexpr (FMT != 0) {
+        const int sy = min(gy, p.NY - 1) >> 1;
+        s = __ldg(p.scale_in + (static_cast<long long>(gz) * p.slabs_y + sy) * p.slabs_x + blockIdx.x);
+      }
+      const float4 u = load_snap4_smem<FMT>(Pst + L::S_OFF + (ty * T::BX + 4 * tx) * L::SNAP_ELEM, s);
+      float4 g = *reinterpret_cast<const float4*>(Pst + L::G_OFF + tofs);
+      g.x -= u.x * (out.x - 2.f * c.x + prev.x) * p.inv_dt2;
+      g.y -= u.y * (out.y - 2.f * c.y + prev.y) * p.inv_dt2;
+      g.z -= u.z * (out.z - 2.f * c.z + prev.z) * p.inv_dt2;
+      g.w -= u.w * (out.w - 2.f * c.w + prev.w) * p.inv_dt2;
+      if (store_ok) *reinterpret_cast<float4*>(p.grad + idx) = g;
+    }
+
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive(&emptyU[uc]);
+      mbar_arrive(&emptyP[ps]);
+    }
+  }
+  if (!ok && lane == 0) {
+    *abort_flag = 1;
+    atomicExch(p.status, kDevTimeout);
+  }
+}
+
+}  // namespace dev
+
+// Host launcher for one radius; instantiated once per step_r<R>.cu.
+template <int R, int NDIM, int MODE>
+static cudaError_t launch_one(const StepMaps& maps, const StepParams& p, dim3 grid, cudaStream_t stream) {
+  using T = StepTraits<R, NDIM>;
+  using L = StepLayout<R, NDIM, MODE>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(dev::step_kernel<R, NDIM, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  dev::step_kernel<R, NDIM, MODE><<<grid, T::NTHREADS, L::SMEM, stream>>>(maps.u, maps.p, maps.cm, maps.g, maps.s, p);
+  return cudaGetLastError();
+}
+
+template <int R, int NDIM>
+static cudaError_t launch_modes(int mode, const StepMaps& maps, const StepParams& p, dim3 grid, cudaStream_t s) {
+  switch (mode) {
+    case MODE_PLAIN: return launch_one<R, NDIM, MODE_PLAIN>(maps, p, grid, s);
+    case MODE_SNAP_F32: return launch_one<R, NDIM, MODE_SNAP_F32>(maps, p, grid, s);
+    case MODE_SNAP_BF16: return launch_one<R, NDIM, MODE_SNAP_BF16>(maps, p, grid, s);
+    case MODE_SNAP_F16: return launch_one<R, NDIM, MODE_SNAP_F16>(maps, p, grid, s);
+    case MODE_GRAD_F32: return launch_one<R, NDIM, MODE_GRAD_F32>(maps, p, grid, s);
+    case MODE_GRAD_BF16: return launch_one<R, NDIM, MODE_GRAD_BF16>(maps, p, grid, s);
+    case MODE_GRAD_F16: return launch_one<R, NDIM, MODE_GRAD_F16>(maps, p, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int R, int NDIM>
+static int smem_modes(int mode) {
+  switch (mode) {
+    case MODE_PLAIN: return StepLayout<R, NDIM, MODE_PLAIN>::SMEM;
+    case MODE_SNAP_F32: return StepLayout<R, NDIM, MODE_SNAP_F32>::SMEM;
+    case MODE_SNAP_BF16: return StepLayout<R, NDIM, MODE_SNAP_BF16>::SMEM;
+    case MODE_SNAP_F16: return StepLayout<R, NDIM, MODE_SNAP_F16>::SMEM;
+    case MODE_GRAD_F32: return StepLayout<R, NDIM, MODE_GRAD_F32>::SMEM;
+    case MODE_GRAD_BF16: return StepLayout<R, NDIM, MODE_GRAD_BF16>::SMEM;
+    case MODE_GRAD_F16: return StepLayout<R, NDIM, MODE_GRAD_F16>::SMEM;
+    default: return -1;
+  }
+}
+
+}  // namespace wave
+
+// Defines the per-radius entry points used by step_dispatch.cu.
+#define WAVE_DEFINE_STEP_RADIUS(RR)                                                                      \
+  namespace wave {                                                                                      \
+  cudaError_t launch_step_r##RR(int ndim, int mode, const StepMaps& maps, const StepParams& p, dim3 grid, \
+                                cudaStream_t s) {                                                       \
+    return ndim == 3 ? launch_modes<RR, 3>(mode, maps, p, grid, s) : launch_modes<RR, 2>(mode, maps, p, grid, s); \
+  }                                                                                                     \
+  int step_smem_r##RR(int ndim, int mode) { return ndim == 3 ? smem_modes<RR, 3>(mode) : smem_modes<RR, 2>(mode); } \
+  }

@@ -1,0 +1,3 @@
+// Stencil step instantiations for radius R = 4 (space order 8).
+#include "step_kernel.cuh"
+WAVE_DEFINE_STEP_RADIUS(4)

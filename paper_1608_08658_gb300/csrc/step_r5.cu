@@ -1,0 +1,3 @@
+// Stencil step instantiations for radius R = 5 (space order 10).
+#include "step_kernel.cuh"
+WAVE_DEFINE_STEP_RADIUS(5)

@@ -1,0 +1,3 @@
+// Stencil step instantiations for radius R = 6 (space order 12).
+#include "step_kernel.cuh"
+WAVE_DEFINE_STEP_RADIUS(6)

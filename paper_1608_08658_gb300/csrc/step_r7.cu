@@ -1,0 +1,3 @@
+// Stencil step instantiations for radius R = 7 (space order 14).
+#include "step_kernel.cuh"
+WAVE_DEFINE_STEP_RADIUS(7)

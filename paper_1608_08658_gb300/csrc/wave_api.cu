@@ -1,0 +1,1295 @@
+// C ABI of the wave library (include/wave.h): argument checking, workspace,
+// host/device staging, sparse-point structures, the forward, adjoint and
+// gradient sweeps and the checkpointed gradient.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "wave.h"
+#include "wave_internal.h"
+
+using namespace wave;
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+
+struct PointSetDev {
+  bool valid = false;
+  uint64_t key = 0;
+  long long n = 0;
+  int ncell = 0;
+  std::string tag;  // workspace name prefix
+  long long* base = nullptr;
+  float* frac = nullptr;
+  long long* cell = nullptr;
+  int* rowptr = nullptr;
+  int* pidx = nullptr;
+  float* w = nullptr;
+  float* coef = nullptr;
+};
+
+struct Pending {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct wave_context {
+  int device = 0;
+  size_t budget = 0;
+  size_t held = 0;
+  std::string err;
+  EncodeTiledFn encode = nullptr;
+  int* d_status = nullptr;
+  int* h_status = nullptr;
+  unsigned int* d_minmax = nullptr;
+  unsigned int* h_minmax = nullptr;
+  double* d_phi = nullptr;
+  double* h_phi = nullptr;
+  std::map<std::string, DevBuf> ws;
+  PointSetDev pts[4];
+  int pts_next = 0;
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<Pending> pending;
+  int64_t launches[WAVE_KERNEL_KINDS] = {};
+  double ms[WAVE_KERNEL_KINDS] = {};
+  int ckpt_interval = 0;
+};
+
+namespace {
+
+int fail(wave_context* ctx, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) {                                                                       \
+      cudaGetLastError();                                                                          \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? WAVE_ERR_OUT_OF_MEMORY : WAVE_ERR_CUDA,  \
+                  "%s failed: %s", #call, cudaGetErrorString(e_));                                 \
+    }                                                                                              \
+  } while (0)
+
+#define TRY(expr)             \
+  do {                        \
+    int rc_ = (expr);         \
+    if (rc_ != WAVE_OK) return rc_; \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int ws_get(wave_context* ctx, const std::string& name, size_t bytes, void** out) {
+  bytes = round_up(std::max<size_t>(bytes, 256), 256);
+  DevBuf& b = ctx->ws[name];
+  if (b.bytes >= bytes) {
+    *out = b.ptr;
+    return WAVE_OK;
+  }
+  const size_t new_held = ctx->held - b.bytes + bytes;
+  if (ctx->budget && new_held > ctx->budget)
+    return fail(ctx, WAVE_ERR_OUT_OF_MEMORY, "workspace '%s' (%zu bytes) would exceed the budget of %zu bytes",
+                name.c_str(), bytes, ctx->budget);
+  if (b.ptr) {
+    cudaFree(b.ptr);
+    ctx->held -= b.bytes;
+    b = DevBuf();
+  }
+  cudaError_t e = cudaMalloc(&b.ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    b = DevBuf();
+    return fail(ctx, WAVE_ERR_OUT_OF_MEMORY, "cudaMalloc of %zu bytes for '%s' failed: %s", bytes, name.c_str(),
+                cudaGetErrorString(e));
+  }
+  b.bytes = bytes;
+  ctx->held += bytes;
+  *out = b.ptr;
+  return WAVE_OK;
+}
+
+void ws_release(wave_context* ctx, const std::string& name) {
+  auto it = ctx->ws.find(name);
+  if (it == ctx->ws.end()) return;
+  if (it->second.ptr) cudaFree(it->second.ptr);
+  ctx->held -= it->second.bytes;
+  ctx->ws.erase(it);
+}
+
+size_t ws_size(wave_context* ctx, const std::string& name) {
+  auto it = ctx->ws.find(name);
+  return it == ctx->ws.end() ? 0 : it->second.bytes;
+}
+
+int classify(wave_context* ctx, const void* p, bool* on_device) {
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *on_device = false;
+    return WAVE_OK;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+    if (a.device != ctx->device)
+      return fail(ctx, WAVE_ERR_INVALID_ARG, "device pointer belongs to device %d, context is on %d", a.device,
+                  ctx->device);
+    *on_device = true;
+  } else {
+    *on_device = false;
+  }
+  return WAVE_OK;
+}
+
+// Input array: device pointers are used in place, host arrays are copied into
+// a named workspace buffer on `s`.
+int stage_in(wave_context* ctx, const char* name, const void* p, size_t bytes, cudaStream_t s, const void** out) {
+  if (bytes == 0) {
+    *out = p;
+    return WAVE_OK;
+  }
+  bool dev = false;
+  TRY(classify(ctx, p, &dev));
+  if (dev) {
+    *out = p;
+    return WAVE_OK;
+  }
+  void* d = nullptr;
+  TRY(ws_get(ctx, std::string("in_") + name, bytes, &d));
+  CK(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, s));
+  *out = d;
+  return WAVE_OK;
+}
+
+struct OutStage {
+  void* user = nullptr;
+  void* dev = nullptr;
+  size_t bytes = 0;
+  bool copy_back = false;
+};
+
+int stage_out(wave_context* ctx, const char* name, void* p, size_t bytes, OutStage* o) {
+  o->user = p;
+  o->bytes = bytes;
+  if (p == nullptr || bytes == 0) {
+    o->dev = nullptr;
+    return WAVE_OK;
+  }
+  bool dev = false;
+  TRY(classify(ctx, p, &dev));
+  if (dev) {
+    o->dev = p;
+    return WAVE_OK;
+  }
+  TRY(ws_get(ctx, std::string("out_") + name, bytes, &o->dev));
+  o->copy_back = true;
+  return WAVE_OK;
+}
+
+int finish_out(wave_context* ctx, const OutStage& o, cudaStream_t s) {
+  if (o.copy_back) CK(cudaMemcpyAsync(o.user, o.dev, o.bytes, cudaMemcpyDeviceToHost, s));
+  return WAVE_OK;
+}
+
+// ---------------------------------------------------------------- profiling
+cudaEvent_t take_event(wave_context* ctx) {
+  if (!ctx->ev_free.empty()) {
+    cudaEvent_t e = ctx->ev_free.back();
+    ctx->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+template <class F>
+int launch(wave_context* ctx, int kind, cudaStream_t s, F&& f) {
+  ctx->launches[kind]++;
+  cudaError_t e;
+  if (ctx->profiling) {
+    Pending pd{kind, take_event(ctx), take_event(ctx)};
+    cudaEventRecord(pd.a, s);
+    e = f();
+    cudaEventRecord(pd.b, s);
+    ctx->pending.push_back(pd);
+  } else {
+    e = f();
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, WAVE_ERR_CUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+  }
+  return WAVE_OK;
+}
+
+void collect_events(wave_context* ctx) {
+  for (auto& pd : ctx->pending) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, pd.a, pd.b) == cudaSuccess) ctx->ms[pd.kind] += t;
+    cudaGetLastError();
+    ctx->ev_free.push_back(pd.a);
+    ctx->ev_free.push_back(pd.b);
+  }
+  ctx->pending.clear();
+}
+
+// ---------------------------------------------------------------- problem set-up
+double fd_weight(int R, int j) {
+  if (j == 0) {
+    double s = 0;
+    for (int k = 1; k <= R; ++k) s += 1.0 / (double(k) * k);
+    return -2.0 * s;
+  }
+  // 2 (-1)^{j+1} (R!)^2 / (j^2 (R-j)! (R+j)!) = 2 (-1)^{j+1} / j^2 * prod_{i=1..j} (R-j+i)/(R+i)
+  double r = 1.0;
+  for (int i = 1; i <= j; ++i) r *= double(R - j + i) / double(R + i);
+  return 2.0 * ((j % 2) ? 1.0 : -1.0) * r / (double(j) * j);
+}
+
+bool valid_order(int so) { return so >= 2 && so <= 16 && so % 2 == 0; }
+
+double dt_limit(int ndim, const double* h, int so, double vmax) {
+  const int R = so / 2;
+  double abs_sum = std::fabs(fd_weight(R, 0));
+  for (int j = 1; j <= R; ++j) abs_sum += 2.0 * std::fabs(fd_weight(R, j));
+  double lam = 0;
+  for (int d = 0; d < ndim; ++d) lam += abs_sum / (h[d] * h[d]);
+  return 2.0 / (vmax * std::sqrt(lam));
+}
+
+struct Prob {
+  int ndim = 0, so = 0, R = 0, nt = 0;
+  float dt = 0;
+  GridDims g{};
+  double h[3] = {0, 0, 0};       // spacing per kernel axis
+  double o[3] = {0, 0, 0};       // computational origin per kernel axis
+  double lo[3] = {0, 0, 0};      // physical extent per kernel axis
+  double hi[3] = {0, 0, 0};
+  int n[3] = {1, 1, 1};          // computational points per kernel axis
+  long long slot_elems = 0;      // NZ*NY*pitch
+  long long phys_elems = 0;      // PZ*PY*PX
+  long long dense_elems = 0;     // NZ*NY*NX
+  int slabs_x = 0, slabs_y = 0;
+  long long scale_elems = 0;     // slabs per level
+  float em[3] = {0, 0, 0};       // eta_max/nbl^2 per kernel axis
+  StepParams sp{};
+  dim3 grid;
+};
+
+int prepare(wave_context* ctx, const wave_geometry* geom, float dt, int nt, int so, Prob* P) {
+  if (!geom) return fail(ctx, WAVE_ERR_INVALID_ARG, "geometry is NULL");
+  if (geom->ndim != 2 && geom->ndim != 3) return fail(ctx, WAVE_ERR_INVALID_ARG, "ndim must be 2 or 3");
+  if (!valid_order(so)) return fail(ctx, WAVE_ERR_INVALID_ARG, "space_order must be even in [2, 16], got %d", so);
+  if (nt < 2) return fail(ctx, WAVE_ERR_INVALID_ARG, "nt must be >= 2, got %d", nt);
+  if (!(dt > 0.f) || !std::isfinite(dt)) return fail(ctx, WAVE_ERR_INVALID_ARG, "dt must be positive and finite");
+  if (geom->nbl < 0) return fail(ctx, WAVE_ERR_INVALID_ARG, "nbl must be >= 0");
+  if (geom->nbl > 0 && !(geom->sponge_vref > 0)) return fail(ctx, WAVE_ERR_INVALID_ARG, "sponge_vref must be > 0");
+  const int nd = geom->ndim;
+  for (int d = 0; d < nd; ++d) {
+    if (geom->shape[d] < 2 || geom->shape[d] > (1 << 20))
+      return fail(ctx, WAVE_ERR_INVALID_ARG, "shape[%d] = %lld out of range [2, 2^20]", d, (long long)geom->shape[d]);
+    if (!(geom->spacing[d] > 0) || !std::isfinite(geom->spacing[d]))
+      return fail(ctx, WAVE_ERR_INVALID_ARG, "spacing[%d] must be positive", d);
+  }
+  P->ndim = nd;
+  P->so = so;
+  P->R = so / 2;
+  P->nt = nt;
+  P->dt = dt;
+  const int nbl = geom->nbl;
+  GridDims& g = P->g;
+  // kernel axes: 3D (x, y, z); 2D (x, depth, -)
+  for (int a = 0; a < 3; ++a) {
+    if (a < nd) {
+      P->n[a] = static_cast<int>(geom->shape[a] + 2 * nbl);
+      P->h[a] = geom->spacing[a];
+      P->o[a] = geom->origin[a] - nbl * geom->spacing[a];
+      P->lo[a] = geom->origin[a];
+      P->hi[a] = geom->origin[a] + (geom->shape[a] - 1) * geom->spacing[a];
+    } else {
+      P->n[a] = 1;
+      P->h[a] = 1.0;
+    }
+  }
+  g.NX = P->n[0];
+  g.NY = P->n[1];
+  g.NZ = P->n[2];
+  g.pitch = static_cast<int>(round_up(g.NX, 8));
+  g.nblx = nbl;
+  g.nbly = nbl;
+  g.nblz = nd == 3 ? nbl : 0;
+  g.PX = static_cast<int>(geom->shape[0]);
+  g.PY = static_cast<int>(geom->shape[1]);
+  g.PZ = nd == 3 ? static_cast<int>(geom->shape[2]) : 1;
+  P->slot_elems = static_cast<long long>(g.NZ) * g.NY * g.pitch;
+  P->phys_elems = static_cast<long long>(g.PZ) * g.PY * g.PX;
+  P->dense_elems = static_cast<long long>(g.NZ) * g.NY * g.NX;
+  P->slabs_x = (g.NX + kSlabX - 1) / kSlabX;
+  P->slabs_y = (g.NY + kSlabY - 1) / kSlabY;
+  P->scale_elems = static_cast<long long>(P->slabs_x) * P->slabs_y * g.NZ;
+  for (int a = 0; a < nd; ++a) {
+    if (nbl > 0) {
+      const double emax = 3.0 * geom->sponge_vref * std::log(1000.0) / (2.0 * nbl * geom->spacing[a]);
+      P->em[a] = static_cast<float>(emax / (double(nbl) * nbl));
+    }
+  }
+  // stencil coefficients with 1/h^2 folded in
+  StepParams& sp = P->sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.NX = g.NX;
+  sp.NY = g.NY;
+  sp.NZ = g.NZ;
+  sp.pitch = g.pitch;
+  sp.slot_elems = P->slot_elems;
+  double inv_h2[3];
+  for (int a = 0; a < 3; ++a) inv_h2[a] = (a < nd) ? 1.0 / (P->h[a] * P->h[a]) : 0.0;
+  sp.c0 = static_cast<float>(fd_weight(P->R, 0) * (inv_h2[0] + inv_h2[1] + inv_h2[2]));
+  for (int j = 1; j <= P->R; ++j) {
+    const double w = fd_weight(P->R, j);
+    sp.cx[j - 1] = static_cast<float>(w * inv_h2[0]);
+    sp.cy[j - 1] = static_cast<float>(w * inv_h2[1]);
+    sp.cz[j - 1] = static_cast<float>(w * inv_h2[2]);
+  }
+  sp.nblx = g.nblx;
+  sp.nbly = g.nbly;
+  sp.nblz = g.nblz;
+  sp.emx = P->em[0];
+  sp.emy = P->em[1];
+  sp.emz = P->em[2];
+  sp.half_inv_dt = static_cast<float>(0.5 / double(dt));
+  sp.inv_dt2 = static_cast<float>(1.0 / (double(dt) * dt));
+  sp.slabs_x = P->slabs_x;
+  sp.slabs_y = P->slabs_y;
+  sp.status = ctx->d_status;
+  // grid: x tiles, axis-1 tiles, chunks of the streamed axis
+  const int tx = (g.NX + step_bx() - 1) / step_bx();
+  const int ty = (g.NY + step_by(P->R, nd) - 1) / step_by(P->R, nd);
+  int chunks = 1;
+  if (nd == 3) {
+    const long long tiles = static_cast<long long>(tx) * ty;
+    const long long target = 8LL * 152;
+    chunks = static_cast<int>(std::max<long long>(1, (target + tiles - 1) / tiles));
+    const int min_len = std::max(16, 4 * P->R);
+    chunks = std::min(chunks, std::max(1, g.NZ / min_len));
+  }
+  sp.zchunk = (g.NZ + chunks - 1) / chunks;
+  chunks = (g.NZ + sp.zchunk - 1) / sp.zchunk;
+  if (ty > 65535 || chunks > 65535) return fail(ctx, WAVE_ERR_NOT_SUPPORTED, "grid too large for one launch");
+  P->grid = dim3(tx, ty, chunks);
+  return WAVE_OK;
+}
+
+int make_map(wave_context* ctx, CUtensorMap* map, CUtensorMapDataType dtype, int rank, const void* base,
+             const cuuint64_t* dims, const cuuint64_t* strides, const cuuint32_t* box) {
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  CUresult r = ctx->encode(map, dtype, rank, const_cast<void*>(base), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(ctx, WAVE_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return WAVE_OK;
+}
+
+struct Work {
+  float* fields = nullptr;  // 4 slots
+  float* cm = nullptr;
+  float* grad = nullptr;
+  StepMaps maps;
+};
+
+// Field buffer, coefficient field and their tensor maps.
+int prepare_fields(wave_context* ctx, Prob& P, const float* m_dev, cudaStream_t s, bool need_grad, Work* W) {
+  const GridDims& g = P.g;
+  void* p = nullptr;
+  TRY(ws_get(ctx, "fields", 4 * P.slot_elems * sizeof(float), &p));
+  W->fields = static_cast<float*>(p);
+  TRY(ws_get(ctx, "cm", P.slot_elems * sizeof(float), &p));
+  W->cm = static_cast<float*>(p);
+  if (need_grad) {
+    TRY(ws_get(ctx, "grad", P.slot_elems * sizeof(float), &p));
+    W->grad = static_cast<float*>(p);
+  }
+  // model checks: positive, finite, and dt within the stability limit
+  CK(cudaMemsetAsync(ctx->d_minmax, 0, 2 * sizeof(unsigned int), s));
+  CK(cudaMemsetAsync(ctx->d_minmax, 0xff, sizeof(unsigned int), s));
+  TRY(launch(ctx, WAVE_KERNEL_OTHER, s, [&] { return launch_minmax(m_dev, P.phys_elems, ctx->d_minmax, s); }));
+  CK(cudaMemcpyAsync(ctx->h_minmax, ctx->d_minmax, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  float mmin, mmax;
+  std::memcpy(&mmin, &ctx->h_minmax[0], 4);
+  std::memcpy(&mmax, &ctx->h_minmax[1], 4);
+  if (!(mmin > 0.f) || !std::isfinite(mmax) || ctx->h_minmax[0] == 0u)
+    return fail(ctx, WAVE_ERR_INVALID_ARG, "model must be positive and finite (min %g, max %g)", mmin, mmax);
+  const double vmax = 1.0 / std::sqrt(double(mmin));
+  const double dtm = dt_limit(P.ndim, P.h, P.so, vmax);
+  if (double(P.dt) > dtm)
+    return fail(ctx, WAVE_ERR_UNSTABLE_DT, "dt = %g ms exceeds the stability limit %g ms (v_max = %g km/s)",
+                double(P.dt), dtm, vmax);
+  TRY(launch(ctx, WAVE_KERNEL_OTHER, s, [&] {
+    return launch_setup_cm(g, m_dev, W->cm, static_cast<float>(double(P.dt) * P.dt), s);
+  }));
+  // tensor maps
+  const int hx = step_hx(P.R);
+  const int by = step_by(P.R, P.ndim);
+  const int bx = step_bx();
+  {
+    cuuint64_t dims[4] = {(cuuint64_t)g.NX, (cuuint64_t)g.NY, (cuuint64_t)g.NZ, 4};
+    cuuint64_t str[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.pitch * g.NY * 4, (cuuint64_t)P.slot_elems * 4};
+    cuuint32_t boxu[4] = {(cuuint32_t)(bx + 2 * hx), (cuuint32_t)(by + 2 * P.R), 1, 1};
+    cuuint32_t boxp[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, 1};
+    TRY(make_map(ctx, &W->maps.u, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, W->fields, dims, str, boxu));
+    TRY(make_map(ctx, &W->maps.p, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, W->fields, dims, str, boxp));
+  }
+  {
+    cuuint64_t dims[3] = {(cuuint64_t)g.NX, (cuuint64_t)g.NY, (cuuint64_t)g.NZ};
+    cuuint64_t str[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.pitch * g.NY * 4};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    TRY(make_map(ctx, &W->maps.cm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, W->cm, dims, str, box));
+    if (need_grad) TRY(make_map(ctx, &W->maps.g, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, W->grad, dims, str, box));
+    else W->maps.g = W->maps.cm;
+  }
+  W->maps.s = W->maps.p;
+  P.sp.fields = W->fields;
+  P.sp.status = ctx->d_status;
+  return WAVE_OK;
+}
+
+int snapshot_map(wave_context* ctx, Prob& P, int fmt, void* store, int levels, CUtensorMap* map) {
+  const GridDims& g = P.g;
+  const int es = fmt == 0 ? 4 : 2;
+  cuuint64_t dims[4] = {(cuuint64_t)g.NX, (cuuint64_t)g.NY, (cuuint64_t)g.NZ, (cuuint64_t)levels};
+  cuuint64_t str[3] = {(cuuint64_t)g.pitch * es, (cuuint64_t)g.pitch * g.NY * es, (cuuint64_t)P.slot_elems * es};
+  cuuint32_t box[4] = {(cuuint32_t)step_bx(), (cuuint32_t)step_by(P.R, P.ndim), 1, 1};
+  const CUtensorMapDataType dt = fmt == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                          : (fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+  return make_map(ctx, map, dt, 4, store, dims, str, box);
+}
+
+// ---------------------------------------------------------------- sparse points
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+  const unsigned char* c = static_cast<const unsigned char*>(p);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= c[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+int prepare_points(wave_context* ctx, Prob& P, const wave_points* pts, cudaStream_t s, PointSetDev** out) {
+  if (!pts) return fail(ctx, WAVE_ERR_INVALID_ARG, "point set is NULL");
+  const long long n = pts->n;
+  if (n < 0 || n > (1LL << 28)) return fail(ctx, WAVE_ERR_INVALID_ARG, "point count %lld out of range", n);
+  if (n > 0 && !pts->coords) return fail(ctx, WAVE_ERR_INVALID_ARG, "point coordinates are NULL");
+  const int nd = P.ndim;
+  std::vector<float> c(static_cast<size_t>(n) * nd);
+  if (n > 0) {
+    bool dev = false;
+    TRY(classify(ctx, pts->coords, &dev));
+    if (dev) CK(cudaMemcpy(c.data(), pts->coords, c.size() * sizeof(float), cudaMemcpyDeviceToHost));
+    else std::memcpy(c.data(), pts->coords, c.size() * sizeof(float));
+  }
+  uint64_t key = 1469598103934665603ull;
+  key = fnv(key, c.data(), c.size() * sizeof(float));
+  key = fnv(key, &n, sizeof(n));
+  key = fnv(key, &P.g, sizeof(P.g));
+  key = fnv(key, P.h, sizeof(P.h));
+  key = fnv(key, P.o, sizeof(P.o));
+  key = fnv(key, P.lo, sizeof(P.lo));
+  key = fnv(key, P.hi, sizeof(P.hi));
+  for (auto& e : ctx->pts) {
+    if (e.valid && e.key == key && e.n == n) {
+      *out = &e;
+      return WAVE_OK;
+    }
+  }
+  const GridDims& g = P.g;
+  const long long sy = g.pitch, sz = static_cast<long long>(g.pitch) * g.NY;
+  std::vector<long long> base(static_cast<size_t>(n));
+  std::vector<float> frac(static_cast<size_t>(n) * 3, 0.f);
+  struct Trip {
+    long long cell;
+    int p;
+    float w;
+  };
+  const int C = 1 << nd;
+  std::vector<Trip> trips;
+  trips.reserve(static_cast<size_t>(n) * C);
+  for (long long i = 0; i < n; ++i) {
+    long long b = 0;
+    double f[3] = {0, 0, 0};
+    for (int a = 0; a < nd; ++a) {
+      const double x = c[i * nd + a];
+      if (!(x >= P.lo[a] && x <= P.hi[a]))
+        return fail(ctx, WAVE_ERR_POINT_OUTSIDE, "point %lld axis %d coordinate %g outside [%g, %g]", i, a, x,
+                    P.lo[a], P.hi[a]);
+      const double t = (x - P.o[a]) / P.h[a];
+      long long k = static_cast<long long>(std::floor(t));
+      if (k >= P.n[a] - 1) k = P.n[a] - 2;
+      if (k < 0) k = 0;
+      double fr = t - double(k);
+      fr = fr < 0 ? 0 : (fr > 1 ? 1 : fr);
+      f[a] = fr;
+      b += k * (a == 0 ? 1 : (a == 1 ? sy : sz));
+    }
+    base[i] = b;
+    for (int a = 0; a < 3; ++a) frac[i * 3 + a] = static_cast<float>(f[a]);
+    for (int cc = 0; cc < C; ++cc) {
+      double w = 1.0;
+      long long idx = b;
+      for (int a = 0; a < nd; ++a) {
+        const int bit = (cc >> a) & 1;
+        w *= bit ? f[a] : 1.0 - f[a];
+        idx += bit ? (a == 0 ? 1 : (a == 1 ? sy : sz)) : 0;
+      }
+      trips.push_back({idx, static_cast<int>(i), static_cast<float>(w)});
+    }
+  }
+  std::sort(trips.begin(), trips.end(), [](const Trip& x, const Trip& y) {
+    return x.cell < y.cell || (x.cell == y.cell && x.p < y.p);
+  });
+  std::vector<long long> cells;
+  std::vector<int> rowptr(1, 0), pidx;
+  std::vector<float> wts;
+  for (size_t k = 0; k < trips.size(); ++k) {
+    if (k == 0 || trips[k].cell != trips[k - 1].cell) {
+      if (k > 0) rowptr.push_back(static_cast<int>(k));
+      cells.push_back(trips[k].cell);
+    }
+    pidx.push_back(trips[k].p);
+    wts.push_back(trips[k].w);
+  }
+  rowptr.push_back(static_cast<int>(trips.size()));
+  if (cells.empty()) rowptr.assign(1, 0);
+  // store in a cache slot
+  PointSetDev& e = ctx->pts[ctx->pts_next];
+  ctx->pts_next = (ctx->pts_next + 1) % 4;
+  e.valid = false;
+  const int slot = static_cast<int>(&e - ctx->pts);
+  e.tag = "pts" + std::to_string(slot) + "_";
+  void* p = nullptr;
+  TRY(ws_get(ctx, e.tag + "base", std::max<size_t>(1, base.size()) * 8, &p));
+  e.base = static_cast<long long*>(p);
+  TRY(ws_get(ctx, e.tag + "frac", std::max<size_t>(1, frac.size()) * 4, &p));
+  e.frac = static_cast<float*>(p);
+  TRY(ws_get(ctx, e.tag + "cell", std::max<size_t>(1, cells.size()) * 8, &p));
+  e.cell = static_cast<long long*>(p);
+  TRY(ws_get(ctx, e.tag + "rowptr", rowptr.size() * 4, &p));
+  e.rowptr = static_cast<int*>(p);
+  TRY(ws_get(ctx, e.tag + "pidx", std::max<size_t>(1, pidx.size()) * 4, &p));
+  e.pidx = static_cast<int*>(p);
+  TRY(ws_get(ctx, e.tag + "w", std::max<size_t>(1, wts.size()) * 4, &p));
+  e.w = static_cast<float*>(p);
+  TRY(ws_get(ctx, e.tag + "coef", std::max<size_t>(1, cells.size()) * 4, &p));
+  e.coef = static_cast<float*>(p);
+  if (n > 0) {
+    CK(cudaMemcpyAsync(e.base, base.data(), base.size() * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(e.frac, frac.data(), frac.size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(e.cell, cells.data(), cells.size() * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(e.pidx, pidx.data(), pidx.size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(e.w, wts.data(), wts.size() * 4, cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemcpyAsync(e.rowptr, rowptr.data(), rowptr.size() * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // host vectors go out of scope
+  e.n = n;
+  e.ncell = static_cast<int>(cells.size());
+  e.key = key;
+  e.valid = true;
+  *out = &e;
+  return WAVE_OK;
+}
+
+GatherSet gather_set(const Prob& P, const PointSetDev* ps) {
+  GatherSet gs;
+  gs.n = ps->n;
+  gs.base = ps->base;
+  gs.frac = ps->frac;
+  gs.ndim = P.ndim;
+  gs.sy = P.g.pitch;
+  gs.sz = static_cast<long long>(P.g.pitch) * P.g.NY;
+  return gs;
+}
+
+InjectSet inject_set(const PointSetDev* ps) {
+  InjectSet is;
+  is.n = ps->ncell;
+  is.cell = ps->cell;
+  is.rowptr = ps->rowptr;
+  is.pidx = ps->pidx;
+  is.w = ps->w;
+  is.coef = ps->coef;
+  return is;
+}
+
+int inject_coefficients(wave_context* ctx, Prob& P, Work& W, PointSetDev* ps, cudaStream_t s) {
+  InjectSet is = inject_set(ps);
+  return launch(ctx, WAVE_KERNEL_OTHER, s,
+                [&] { return launch_inject_coef(is, P.g, W.cm, P.em, P.sp.half_inv_dt, s); });
+}
+
+// ---------------------------------------------------------------- sweeps
+inline int fslot(int n) { return n & 1; }            // forward level n lives in slot n&1 (u^{-1} in slot 1)
+inline int aslot(int j) { return 2 + (j & 1); }      // adjoint level j lives in slot 2 + (j&1)
+
+float* slot_ptr(Work& W, const Prob& P, int slot) { return W.fields + slot * P.slot_elems; }
+
+int step(wave_context* ctx, Prob& P, Work& W, int mode, int cur, int prev, cudaStream_t s) {
+  P.sp.cur = cur;
+  P.sp.prev = prev;
+  const int kind = mode_is_grad(mode) ? WAVE_KERNEL_STEP_GRAD
+                                      : (mode_is_snap(mode) ? WAVE_KERNEL_STEP_SNAP : WAVE_KERNEL_STEP);
+  return launch(ctx, kind, s, [&] { return launch_step(P.R, P.ndim, mode, W.maps, P.sp, P.grid, s); });
+}
+
+struct SnapStore {
+  int fmt = 0;            // 0 f32, 1 bf16, 2 f16
+  int levels = 0;
+  void* data = nullptr;
+  float* scale = nullptr;
+  CUtensorMap map;
+  size_t level_bytes(const Prob& P) const { return static_cast<size_t>(P.slot_elems) * (fmt == 0 ? 4 : 2); }
+  void* level(const Prob& P, int k) const { return static_cast<char*>(data) + level_bytes(P) * k; }
+  float* level_scale(const Prob& P, int k) const { return scale ? scale + P.scale_elems * k : nullptr; }
+};
+
+int alloc_snapshots(wave_context* ctx, Prob& P, int fmt, int levels, SnapStore* S) {
+  S->fmt = fmt;
+  S->levels = levels;
+  void* p = nullptr;
+  TRY(ws_get(ctx, "snap", S->level_bytes(P) * levels, &p));
+  S->data = p;
+  if (fmt != 0) {
+    TRY(ws_get(ctx, "snap_scale", static_cast<size_t>(P.scale_elems) * levels * 4, &p));
+    S->scale = static_cast<float*>(p);
+  } else {
+    S->scale = nullptr;
+  }
+  return snapshot_map(ctx, P, fmt, S->data, levels, &S->map);
+}
+
+// Forward steps n = n0 .. n1-1 (each produces u^{n+1}); q rows injected; receiver
+// rows gathered when d is given; centre levels n >= snap_from stored at
+// level n - snap_base when S is given.
+int forward_steps(wave_context* ctx, Prob& P, Work& W, int n0, int n1, const float* q, PointSetDev* src,
+                  float* d, PointSetDev* rec, SnapStore* S, int snap_from, int snap_base, cudaStream_t s) {
+  InjectSet isrc = inject_set(src);
+  GatherSet grec = rec ? gather_set(P, rec) : GatherSet{};
+  for (int n = n0; n < n1; ++n) {
+    int mode = MODE_PLAIN;
+    if (S && n >= snap_from) {
+      mode = S->fmt == 0 ? MODE_SNAP_F32 : (S->fmt == 1 ? MODE_SNAP_BF16 : MODE_SNAP_F16);
+      P.sp.snap_out = S->level(P, n - snap_base);
+      P.sp.scale_out = S->level_scale(P, n - snap_base);
+    }
+    TRY(step(ctx, P, W, mode, fslot(n), fslot(n - 1), s));
+    float* out = slot_ptr(W, P, fslot(n + 1));
+    if (isrc.n > 0) {
+      const float* row = q + static_cast<long long>(n) * src->n;
+      TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_inject(isrc, row, out, s); }));
+    }
+    if (rec && rec->n > 0 && d) {
+      float* row = d + static_cast<long long>(n + 1) * rec->n;
+      TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_gather(grec, out, row, s); }));
+    }
+  }
+  return WAVE_OK;
+}
+
+int store_level(wave_context* ctx, Prob& P, Work& W, int slot, SnapStore* S, int k, cudaStream_t s) {
+  return launch(ctx, WAVE_KERNEL_OTHER, s, [&] {
+    return launch_snapshot_store(P.g, slot_ptr(W, P, slot), S->level(P, k), S->level_scale(P, k), S->fmt, P.slabs_x,
+                                 P.slabs_y, s);
+  });
+}
+
+// Adjoint-with-gradient iterations j = j1 .. j0 (descending); snapshot of u^j
+// at level j - snap_base.
+int adjoint_grad_steps(wave_context* ctx, Prob& P, Work& W, int j1, int j0, const float* y, PointSetDev* rec,
+                       SnapStore* S, int snap_base, cudaStream_t s) {
+  InjectSet irec = inject_set(rec);
+  const int mode = S->fmt == 0 ? MODE_GRAD_F32 : (S->fmt == 1 ? MODE_GRAD_BF16 : MODE_GRAD_F16);
+  for (int j = j1; j >= j0; --j) {
+    const int lvl = j - snap_base;
+    P.sp.snap_level = lvl;
+    P.sp.scale_in = S->level_scale(P, lvl);
+    P.sp.grad = W.grad;
+    TRY(step(ctx, P, W, mode, aslot(j), aslot(j + 1), s));
+    if (irec.n > 0) {
+      float* out = slot_ptr(W, P, aslot(j - 1));
+      const float* row = y + static_cast<long long>(j) * rec->n;
+      const void* snap = S->level(P, lvl);
+      const float* sc = S->level_scale(P, lvl);
+      TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] {
+        return launch_inject_grad(irec, row, out, W.grad, snap, S->fmt, sc, P.g, P.slabs_x, P.slabs_y, P.sp.inv_dt2,
+                                  s);
+      }));
+    }
+  }
+  return WAVE_OK;
+}
+
+int begin_call(wave_context* ctx) {
+  if (!ctx) return WAVE_ERR_INVALID_ARG;
+  ctx->err.clear();
+  return WAVE_OK;
+}
+
+// Synchronise, read the device status word, collect profiling events.
+int end_call(wave_context* ctx, cudaStream_t s, int rc) {
+  cudaError_t e1 = cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  collect_events(ctx);
+  if (rc != WAVE_OK) {
+    cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    return rc;
+  }
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    cudaError_t e = e2 != cudaSuccess ? e2 : e1;
+    cudaGetLastError();
+    return fail(ctx, WAVE_ERR_CUDA, "stream synchronisation failed: %s", cudaGetErrorString(e));
+  }
+  if (*ctx->h_status != kDevOk) {
+    cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s);
+    cudaStreamSynchronize(s);
+    return fail(ctx, WAVE_ERR_TIMEOUT, "a kernel gave up a bounded wait (device status %d)", *ctx->h_status);
+  }
+  return WAVE_OK;
+}
+
+int check_common(wave_context* ctx, const wave_geometry* geom, const float* m) {
+  if (!ctx) return WAVE_ERR_INVALID_ARG;
+  if (!geom || !m) return fail(ctx, WAVE_ERR_INVALID_ARG, "geometry or model is NULL");
+  return WAVE_OK;
+}
+
+// ---------------------------------------------------------------- forward
+int forward_impl(wave_context* ctx, const wave_geometry* geom, const float* m, const wave_points* src,
+                 const float* q, const wave_points* rec, float* d_out, float dt, int nt, int so,
+                 const float* u_init_prev, const float* u_init, float* u_final_prev, float* u_final, cudaStream_t s) {
+  TRY(check_common(ctx, geom, m));
+  Prob P;
+  TRY(prepare(ctx, geom, dt, nt, so, &P));
+  const long long ns = src ? src->n : 0, nr = rec ? rec->n : 0;
+  if (ns > 0 && !q) return fail(ctx, WAVE_ERR_INVALID_ARG, "source traces are NULL");
+  if (nr > 0 && !d_out) return fail(ctx, WAVE_ERR_INVALID_ARG, "receiver output is NULL");
+  const void* mdev;
+  TRY(stage_in(ctx, "m", m, P.phys_elems * 4, s, &mdev));
+  const void* qdev = nullptr;
+  if (ns > 0) TRY(stage_in(ctx, "q", q, static_cast<size_t>(nt) * ns * 4, s, &qdev));
+  Work W;
+  TRY(prepare_fields(ctx, P, static_cast<const float*>(mdev), s, false, &W));
+  wave_points empty{0, nullptr};
+  PointSetDev *S = nullptr, *Rr = nullptr;
+  TRY(prepare_points(ctx, P, src ? src : &empty, s, &S));
+  TRY(prepare_points(ctx, P, rec ? rec : &empty, s, &Rr));
+  OutStage dout;
+  TRY(stage_out(ctx, "d", d_out, static_cast<size_t>(nt) * nr * 4, &dout));
+  TRY(inject_coefficients(ctx, P, W, S, s));
+  // initial state
+  for (int k = 0; k < 2; ++k) {
+    const float* init = k == 0 ? u_init_prev : u_init;
+    float* slot = slot_ptr(W, P, fslot(k - 1));
+    if (init) {
+      const void* dd;
+      TRY(stage_in(ctx, k == 0 ? "u_init_prev" : "u_init", init, P.dense_elems * 4, s, &dd));
+      CK(cudaMemsetAsync(slot, 0, P.slot_elems * 4, s));
+      TRY(launch(ctx, WAVE_KERNEL_OTHER, s,
+                 [&] { return launch_unpack_state(P.g, static_cast<const float*>(dd), slot, s); }));
+    } else {
+      CK(cudaMemsetAsync(slot, 0, P.slot_elems * 4, s));
+    }
+  }
+  float* d = static_cast<float*>(dout.dev);
+  if (nr > 0) {
+    GatherSet grec = gather_set(P, Rr);
+    TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_gather(grec, slot_ptr(W, P, fslot(0)), d, s); }));
+  }
+  TRY(forward_steps(ctx, P, W, 0, nt - 1, static_cast<const float*>(qdev), S, d, Rr, nullptr, 0, 0, s));
+  TRY(finish_out(ctx, dout, s));
+  for (int k = 0; k < 2; ++k) {
+    float* fin = k == 0 ? u_final_prev : u_final;
+    if (!fin) continue;
+    OutStage o;
+    TRY(stage_out(ctx, k == 0 ? "u_final_prev" : "u_final", fin, P.dense_elems * 4, &o));
+    float* slot = slot_ptr(W, P, fslot(nt - 2 + k));
+    TRY(launch(ctx, WAVE_KERNEL_OTHER, s,
+               [&] { return launch_pack_state(P.g, slot, static_cast<float*>(o.dev), s); }));
+    TRY(finish_out(ctx, o, s));
+  }
+  return WAVE_OK;
+}
+
+// ---------------------------------------------------------------- adjoint
+int adjoint_impl(wave_context* ctx, const wave_geometry* geom, const float* m, const wave_points* src,
+                 const wave_points* rec, const float* y, float* q_out, float dt, int nt, int so, cudaStream_t s) {
+  TRY(check_common(ctx, geom, m));
+  Prob P;
+  TRY(prepare(ctx, geom, dt, nt, so, &P));
+  const long long ns = src ? src->n : 0, nr = rec ? rec->n : 0;
+  if (nr > 0 && !y) return fail(ctx, WAVE_ERR_INVALID_ARG, "adjoint source traces are NULL");
+  if (ns > 0 && !q_out) return fail(ctx, WAVE_ERR_INVALID_ARG, "adjoint output is NULL");
+  const void* mdev;
+  TRY(stage_in(ctx, "m", m, P.phys_elems * 4, s, &mdev));
+  const void* ydev = nullptr;
+  if (nr > 0) TRY(stage_in(ctx, "y", y, static_cast<size_t>(nt) * nr * 4, s, &ydev));
+  Work W;
+  TRY(prepare_fields(ctx, P, static_cast<const float*>(mdev), s, false, &W));
+  wave_points empty{0, nullptr};
+  PointSetDev *S = nullptr, *Rr = nullptr;
+  TRY(prepare_points(ctx, P, src ? src : &empty, s, &S));
+  TRY(prepare_points(ctx, P, rec ? rec : &empty, s, &Rr));
+  OutStage qo;
+  TRY(stage_out(ctx, "q_adj", q_out, static_cast<size_t>(nt) * ns * 4, &qo));
+  TRY(inject_coefficients(ctx, P, W, Rr, s));
+  CK(cudaMemsetAsync(slot_ptr(W, P, 2), 0, 2 * P.slot_elems * 4, s));
+  float* qa = static_cast<float*>(qo.dev);
+  if (ns > 0) CK(cudaMemsetAsync(qa + static_cast<long long>(nt - 1) * ns, 0, ns * 4, s));
+  InjectSet irec = inject_set(Rr);
+  GatherSet gsrc = gather_set(P, S);
+  const float* yd = static_cast<const float*>(ydev);
+  for (int j = nt - 1; j >= 1; --j) {
+    TRY(step(ctx, P, W, MODE_PLAIN, aslot(j), aslot(j + 1), s));
+    float* out = slot_ptr(W, P, aslot(j - 1));
+    if (irec.n > 0) {
+      const float* row = yd + static_cast<long long>(j) * nr;
+      TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_inject(irec, row, out, s); }));
+    }
+    if (ns > 0) {
+      float* row = qa + static_cast<long long>(j - 1) * ns;
+      TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_gather(gsrc, out, row, s); }));
+    }
+  }
+  TRY(finish_out(ctx, qo, s));
+  return WAVE_OK;
+}
+
+// ---------------------------------------------------------------- gradient
+int choose_storage(wave_context* ctx, Prob& P, int mode, int* fmt, bool* ckpt, int* interval) {
+  if (mode < WAVE_SNAP_FULL_FP32 || mode > WAVE_SNAP_AUTO) return fail(ctx, WAVE_ERR_INVALID_ARG, "bad snap_mode %d", mode);
+  const int nt = P.nt;
+  const size_t fb = static_cast<size_t>(P.slot_elems) * 4;
+  auto snap_bytes = [&](int f) {
+    return static_cast<size_t>(P.slot_elems) * (f == 0 ? 4 : 2) + (f == 0 ? 0 : static_cast<size_t>(P.scale_elems) * 4);
+  };
+  size_t avail;
+  {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    cudaGetLastError();
+    const size_t have = ws_size(ctx, "snap") + ws_size(ctx, "snap_scale") + ws_size(ctx, "ckpt");
+    avail = fr + have;
+    if (ctx->budget) {
+      const size_t other = ctx->held - have;
+      const size_t cap = ctx->budget > other ? ctx->budget - other : 0;
+      avail = std::min(avail, cap);
+    }
+    avail = static_cast<size_t>(avail * 0.92);
+  }
+  int f = 0;
+  bool c = false;
+  switch (mode) {
+    case WAVE_SNAP_FULL_FP32: f = 0; break;
+    case WAVE_SNAP_FULL_BF16: f = 1; break;
+    case WAVE_SNAP_FULL_FP16: f = 2; break;
+    case WAVE_SNAP_CHECKPOINT_FP32: f = 0; c = true; break;
+    case WAVE_SNAP_CHECKPOINT_BF16: f = 1; c = true; break;
+    case WAVE_SNAP_CHECKPOINT_FP16: f = 2; c = true; break;
+    case WAVE_SNAP_AUTO: f = 0; c = snap_bytes(0) * static_cast<size_t>(nt) > avail; break;
+  }
+  *fmt = f;
+  *ckpt = c;
+  *interval = nt;
+  if (c) {
+    int S = ctx->ckpt_interval;
+    if (S <= 0) {
+      const double sb = static_cast<double>(snap_bytes(f));
+      S = static_cast<int>(std::ceil(std::sqrt(2.0 * fb * nt / sb)));
+      // fewer, longer segments when memory allows (fewer checkpoint copies)
+      while (S < nt && (static_cast<size_t>(2 * S) * snap_bytes(f) +
+                        static_cast<size_t>((nt + 2 * S - 1) / (2 * S)) * 2 * fb) <= avail / 2)
+        S *= 2;
+      S = std::max(1, std::min(S, nt));
+    }
+    *interval = S;
+  }
+  return WAVE_OK;
+}
+
+int gradient_impl(wave_context* ctx, const wave_geometry* geom, const float* m, const wave_points* src,
+                  const float* q, const wave_points* rec, const float* d_obs, const float* y_given,
+                  float* grad_out, double* phi_out, float* resid_out, float* d_out, int snap_mode, float dt, int nt,
+                  int so, cudaStream_t s) {
+  TRY(check_common(ctx, geom, m));
+  if (!grad_out) return fail(ctx, WAVE_ERR_INVALID_ARG, "gradient output is NULL");
+  Prob P;
+  TRY(prepare(ctx, geom, dt, nt, so, &P));
+  const long long ns = src ? src->n : 0, nr = rec ? rec->n : 0;
+  if (ns > 0 && !q) return fail(ctx, WAVE_ERR_INVALID_ARG, "source traces are NULL");
+  if (nr > 0 && !d_obs && !y_given) return fail(ctx, WAVE_ERR_INVALID_ARG, "observed data are NULL");
+  int fmt;
+  bool ckpt;
+  int S;
+  TRY(choose_storage(ctx, P, snap_mode, &fmt, &ckpt, &S));
+  const void* mdev;
+  TRY(stage_in(ctx, "m", m, P.phys_elems * 4, s, &mdev));
+  const void* qdev = nullptr;
+  if (ns > 0) TRY(stage_in(ctx, "q", q, static_cast<size_t>(nt) * ns * 4, s, &qdev));
+  const void* obs = nullptr;
+  if (nr > 0) TRY(stage_in(ctx, y_given ? "y" : "dobs", y_given ? y_given : d_obs, static_cast<size_t>(nt) * nr * 4, s, &obs));
+  Work W;
+  TRY(prepare_fields(ctx, P, static_cast<const float*>(mdev), s, true, &W));
+  wave_points empty{0, nullptr};
+  PointSetDev *Sp = nullptr, *Rr = nullptr;
+  TRY(prepare_points(ctx, P, src ? src : &empty, s, &Sp));
+  TRY(prepare_points(ctx, P, rec ? rec : &empty, s, &Rr));
+  TRY(inject_coefficients(ctx, P, W, Sp, s));
+  TRY(inject_coefficients(ctx, P, W, Rr, s));
+  OutStage gout, rout, dout;
+  TRY(stage_out(ctx, "grad", grad_out, P.phys_elems * 4, &gout));
+  TRY(stage_out(ctx, "resid", resid_out, static_cast<size_t>(nt) * nr * 4, &rout));
+  TRY(stage_out(ctx, "dpred", d_out, static_cast<size_t>(nt) * nr * 4, &dout));
+  void* p = nullptr;
+  TRY(ws_get(ctx, "d_pred", std::max<size_t>(1, static_cast<size_t>(nt) * nr) * 4, &p));
+  float* d = dout.dev ? static_cast<float*>(dout.dev) : static_cast<float*>(p);
+  float* r = nullptr;
+  if (y_given) {
+    r = const_cast<float*>(static_cast<const float*>(obs));
+  } else {
+    TRY(ws_get(ctx, "resid_ws", std::max<size_t>(1, static_cast<size_t>(nt) * nr) * 4, &p));
+    r = rout.dev ? static_cast<float*>(rout.dev) : static_cast<float*>(p);
+  }
+  const float* qd = static_cast<const float*>(qdev);
+  // storage
+  SnapStore SS;
+  const int levels = ckpt ? S : nt - 1;
+  const int nseg = ckpt ? (nt + S - 1) / S : 1;
+  float* ck = nullptr;
+  if (ckpt) {
+    TRY(ws_get(ctx, "ckpt", static_cast<size_t>(nseg) * 2 * P.slot_elems * 4, &p));
+    ck = static_cast<float*>(p);
+  }
+  TRY(alloc_snapshots(ctx, P, fmt, levels, &SS));
+  W.maps.s = SS.map;
+  // forward sweep
+  CK(cudaMemsetAsync(slot_ptr(W, P, 0), 0, 2 * P.slot_elems * 4, s));
+  CK(cudaMemsetAsync(W.grad, 0, P.slot_elems * 4, s));
+  if (nr > 0) {
+    GatherSet grec = gather_set(P, Rr);
+    TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_gather(grec, slot_ptr(W, P, fslot(0)), d, s); }));
+  }
+  if (!ckpt) {
+    // full storage: level j stored at index j-1, j = 1..nt-1
+    TRY(forward_steps(ctx, P, W, 0, nt - 1, qd, Sp, d, Rr, &SS, 1, 1, s));
+    TRY(store_level(ctx, P, W, fslot(nt - 1), &SS, nt - 2, s));
+  } else {
+    for (int seg = 0; seg < nseg; ++seg) {
+      const int L0 = seg * S;
+      // checkpoint (u^{L0-1}, u^{L0})
+      float* c0 = ck + static_cast<long long>(seg) * 2 * P.slot_elems;
+      CK(cudaMemcpyAsync(c0, slot_ptr(W, P, fslot(L0 - 1)), P.slot_elems * 4, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(c0 + P.slot_elems, slot_ptr(W, P, fslot(L0)), P.slot_elems * 4, cudaMemcpyDeviceToDevice, s));
+      const int L1 = std::min(L0 + S, nt);
+      TRY(forward_steps(ctx, P, W, L0, std::min(L1, nt - 1), qd, Sp, d, Rr, nullptr, 0, 0, s));
+    }
+  }
+  // residual and objective
+  if (nr > 0 && !y_given) {
+    const long long n = static_cast<long long>(nt) * nr;
+    const int nb = residual_blocks(n);
+    TRY(ws_get(ctx, "partials", nb * sizeof(double), &p));
+    double* part = static_cast<double*>(p);
+    const float* dobs = static_cast<const float*>(obs);
+    TRY(launch(ctx, WAVE_KERNEL_OTHER, s, [&] { return launch_residual(d, dobs, r, n, part, nb, s); }));
+    TRY(launch(ctx, WAVE_KERNEL_OTHER, s, [&] { return launch_sum_partials(part, nb, ctx->d_phi, s); }));
+  } else {
+    CK(cudaMemsetAsync(ctx->d_phi, 0, sizeof(double), s));
+  }
+  // adjoint sweep with the imaging condition
+  CK(cudaMemsetAsync(slot_ptr(W, P, 2), 0, 2 * P.slot_elems * 4, s));
+  if (!ckpt) {
+    TRY(adjoint_grad_steps(ctx, P, W, nt - 1, 1, r, Rr, &SS, 1, s));
+  } else {
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+      const int L0 = seg * S;
+      const int L1 = std::min(L0 + S, nt);
+      float* c0 = ck + static_cast<long long>(seg) * 2 * P.slot_elems;
+      CK(cudaMemcpyAsync(slot_ptr(W, P, fslot(L0 - 1)), c0, P.slot_elems * 4, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(slot_ptr(W, P, fslot(L0)), c0 + P.slot_elems, P.slot_elems * 4, cudaMemcpyDeviceToDevice, s));
+      // recompute u^{L0} .. u^{L1-1}, storing level n at index n - L0
+      TRY(forward_steps(ctx, P, W, L0, L1 - 1, qd, Sp, nullptr, nullptr, &SS, L0, L0, s));
+      TRY(store_level(ctx, P, W, fslot(L1 - 1), &SS, L1 - 1 - L0, s));
+      const int jlo = std::max(L0, 1);
+      if (L1 - 1 >= jlo) TRY(adjoint_grad_steps(ctx, P, W, L1 - 1, jlo, r, Rr, &SS, L0, s));
+    }
+  }
+  TRY(launch(ctx, WAVE_KERNEL_OTHER, s,
+             [&] { return launch_fold(P.g, W.grad, static_cast<float*>(gout.dev), s); }));
+  TRY(finish_out(ctx, gout, s));
+  if (!y_given) TRY(finish_out(ctx, rout, s));
+  TRY(finish_out(ctx, dout, s));
+  CK(cudaMemcpyAsync(ctx->h_phi, ctx->d_phi, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (phi_out) *phi_out = *ctx->h_phi;
+  return WAVE_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+// Public entry points
+// ============================================================================
+extern "C" {
+
+int wave_context_create(wave_context** out, int device, size_t hbm_budget_bytes) {
+  if (!out) return WAVE_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return WAVE_ERR_CUDA;
+  }
+  DeviceGuard guard(device);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return WAVE_ERR_CUDA;
+  if (prop.major * 10 + prop.minor != 103) return WAVE_ERR_NOT_SUPPORTED;  // kernels are built for sm_103a only
+  wave_context* ctx = new wave_context();
+  ctx->device = device;
+  ctx->budget = hbm_budget_bytes;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    delete ctx;
+    return WAVE_ERR_CUDA;
+  }
+  ctx->encode = reinterpret_cast<EncodeTiledFn>(fn);
+  bool ok = cudaMalloc(&ctx->d_status, 16) == cudaSuccess && cudaMalloc(&ctx->d_minmax, 16) == cudaSuccess &&
+            cudaMalloc(&ctx->d_phi, 16) == cudaSuccess &&
+            cudaMallocHost(&ctx->h_status, 16) == cudaSuccess && cudaMallocHost(&ctx->h_minmax, 16) == cudaSuccess &&
+            cudaMallocHost(&ctx->h_phi, 16) == cudaSuccess;
+  if (ok) ok = cudaMemset(ctx->d_status, 0, 16) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    wave_context_destroy(ctx);
+    return WAVE_ERR_CUDA;
+  }
+  *out = ctx;
+  return WAVE_OK;
+}
+
+int wave_context_destroy(wave_context* ctx) {
+  if (!ctx) return WAVE_OK;
+  DeviceGuard guard(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : ctx->ws)
+    if (kv.second.ptr) cudaFree(kv.second.ptr);
+  for (auto e : ctx->ev_free) cudaEventDestroy(e);
+  for (auto& pd : ctx->pending) {
+    cudaEventDestroy(pd.a);
+    cudaEventDestroy(pd.b);
+  }
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->d_minmax) cudaFree(ctx->d_minmax);
+  if (ctx->d_phi) cudaFree(ctx->d_phi);
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  if (ctx->h_minmax) cudaFreeHost(ctx->h_minmax);
+  if (ctx->h_phi) cudaFreeHost(ctx->h_phi);
+  cudaGetLastError();
+  delete ctx;
+  return WAVE_OK;
+}
+
+size_t wave_context_workspace_bytes(const wave_context* ctx) { return ctx ? ctx->held : 0; }
+
+int wave_context_trim(wave_context* ctx) {
+  if (!ctx) return WAVE_ERR_INVALID_ARG;
+  DeviceGuard guard(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto& kv : ctx->ws)
+    if (kv.second.ptr) cudaFree(kv.second.ptr);
+  ctx->ws.clear();
+  ctx->held = 0;
+  for (auto& e : ctx->pts) e.valid = false;
+  return WAVE_OK;
+}
+
+int wave_context_set_checkpoint_interval(wave_context* ctx, int steps) {
+  if (!ctx || steps < 0) return WAVE_ERR_INVALID_ARG;
+  ctx->ckpt_interval = steps;
+  return WAVE_OK;
+}
+
+const char* wave_error_string(int status) {
+  switch (status) {
+    case WAVE_OK: return "success";
+    case WAVE_ERR_INVALID_ARG: return "invalid argument";
+    case WAVE_ERR_POINT_OUTSIDE: return "point outside the physical domain";
+    case WAVE_ERR_UNSTABLE_DT: return "time step above the stability limit";
+    case WAVE_ERR_OUT_OF_MEMORY: return "out of device memory or workspace budget";
+    case WAVE_ERR_CUDA: return "CUDA error";
+    case WAVE_ERR_TIMEOUT: return "device-side wait timed out";
+    case WAVE_ERR_NOT_SUPPORTED: return "not supported";
+    default: return "unknown status";
+  }
+}
+
+const char* wave_last_error(const wave_context* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int wave_forward_ex(wave_context* ctx, const wave_geometry* geom, const float* m, const wave_points* src,
+                    const float* q, const wave_points* rec, float* d_out, float dt, int nt, int space_order,
+                    const float* u_init_prev, const float* u_init, float* u_final_prev, float* u_final, void* stream) {
+  TRY(begin_call(ctx));
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = forward_impl(ctx, geom, m, src, q, rec, d_out, dt, nt, space_order, u_init_prev, u_init, u_final_prev,
+                        u_final, s);
+  return end_call(ctx, s, rc);
+}
+
+int wave_forward(wave_context* ctx, const wave_geometry* geom, const float* m, const wave_points* src,
+                 const float* q, const wave_points* rec, float* d_out, float dt, int nt, int space_order,
+                 void* stream) {
+  return wave_forward_ex(ctx, geom, m, src, q, rec, d_out, dt, nt, space_order, nullptr, nullptr, nullptr, nullptr,
+                         stream);
+}
+
+int wave_adjoint(wave_context* ctx, const wave_geometry* geom, const float* m, const wave_points* src,
+                 const wave_points* rec, const float* y, float* q_out, float dt, int nt, int space_order,
+                 void* stream) {
+  TRY(begin_call(ctx));
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = adjoint_impl(ctx, geom, m, src, rec, y, q_out, dt, nt, space_order, s);
+  return end_call(ctx, s, rc);
+}
+
+int wave_gradient(wave_context* ctx, const wave_geometry* geom, const float* m, const wave_points* src,
+                  const float* q, const wave_points* rec, const float* d_obs, float* grad_out, double* phi_out,
+                  float* resid_out, int snap_mode, float dt, int nt, int space_order, void* stream) {
+  TRY(begin_call(ctx));
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = gradient_impl(ctx, geom, m, src, q, rec, d_obs, nullptr, grad_out, phi_out, resid_out, nullptr, snap_mode,
+                         dt, nt, space_order, s);
+  return end_call(ctx, s, rc);
+}
+
+int wave_jacobian_adjoint(wave_context* ctx, const wave_geometry* geom, const float* m, const wave_points* src,
+                          const float* q, const wave_points* rec, const float* y, float* grad_out, float* d_out,
+                          int snap_mode, float dt, int nt, int space_order, void* stream) {
+  TRY(begin_call(ctx));
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long nr = rec ? rec->n : 0;
+  if (nr > 0 && !y) return end_call(ctx, s, fail(ctx, WAVE_ERR_INVALID_ARG, "adjoint source traces are NULL"));
+  int rc = gradient_impl(ctx, geom, m, src, q, rec, nullptr, y, grad_out, nullptr, nullptr, d_out, snap_mode, dt, nt,
+                         space_order, s);
+  return end_call(ctx, s, rc);
+}
+
+int wave_fd_weights(int space_order, double* w_out) {
+  if (!valid_order(space_order) || !w_out) return WAVE_ERR_INVALID_ARG;
+  const int R = space_order / 2;
+  for (int j = 0; j <= R; ++j) w_out[j] = fd_weight(R, j);
+  return WAVE_OK;
+}
+
+double wave_dt_max(int ndim, const double* spacing, int space_order, double v_max) {
+  if ((ndim != 2 && ndim != 3) || !spacing || !valid_order(space_order) || !(v_max > 0)) return -1.0;
+  for (int d = 0; d < ndim; ++d)
+    if (!(spacing[d] > 0)) return -1.0;
+  return dt_limit(ndim, spacing, space_order, v_max);
+}
+
+int wave_ricker(float* q_out, int nt, float dt, float f0, float t0) {
+  if (!q_out || nt < 1 || !(dt > 0) || !(f0 > 0)) return WAVE_ERR_INVALID_ARG;
+  std::vector<float> h(nt);
+  const double pi = 3.14159265358979323846;
+  for (int n = 0; n < nt; ++n) {
+    const double a = pi * f0 * (n * double(dt) - t0);
+    const double a2 = a * a;
+    h[n] = static_cast<float>((1.0 - 2.0 * a2) * std::exp(-a2));
+  }
+  cudaPointerAttributes at;
+  bool dev = cudaPointerGetAttributes(&at, q_out) == cudaSuccess &&
+             (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+  cudaGetLastError();
+  if (dev) {
+    if (cudaMemcpy(q_out, h.data(), nt * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      return WAVE_ERR_CUDA;
+    }
+  } else {
+    std::memcpy(q_out, h.data(), nt * sizeof(float));
+  }
+  return WAVE_OK;
+}
+
+int wave_context_set_profiling(wave_context* ctx, int enable) {
+  if (!ctx) return WAVE_ERR_INVALID_ARG;
+  ctx->profiling = enable != 0;
+  return WAVE_OK;
+}
+
+int wave_context_kernel_stats(wave_context* ctx, int kind, int64_t* launches, double* total_ms) {
+  if (!ctx || kind >= WAVE_KERNEL_KINDS) return WAVE_ERR_INVALID_ARG;
+  int64_t l = 0;
+  double t = 0;
+  for (int k = 0; k < WAVE_KERNEL_KINDS; ++k) {
+    if (kind < 0 || k == kind) {
+      l += ctx->launches[k];
+      t += ctx->ms[k];
+    }
+  }
+  if (launches) *launches = l;
+  if (total_ms) *total_ms = t;
+  return WAVE_OK;
+}
+
+int wave_context_reset_stats(wave_context* ctx) {
+  if (!ctx) return WAVE_ERR_INVALID_ARG;
+  for (int k = 0; k < WAVE_KERNEL_KINDS; ++k) {
+    ctx->launches[k] = 0;
+    ctx->ms[k] = 0;
+  }
+  return WAVE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,185 @@
+// Internal declarations shared by the CUDA translation units of libwave.
+// Not part of the public ABI (see include/wave.h).
+#pragma once
+
+#include <cuda.h>            // CUtensorMap type only; the driver is reached through an entry point
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wave {
+
+// ---------------------------------------------------------------------------
+// Device status word (written by kernels that give up a bounded wait).
+// ---------------------------------------------------------------------------
+constexpr int kDevOk = 0;
+constexpr int kDevTimeout = 1;
+
+// Bounded waits: a kernel gives up after this many nanoseconds of waiting on
+// one barrier phase, records kDevTimeout and returns.
+constexpr unsigned long long kWaitLimitNs = 10ull * 1000ull * 1000ull * 1000ull;
+
+// ---------------------------------------------------------------------------
+// Epilogue variants of the stencil step.
+// ---------------------------------------------------------------------------
+enum StepMode : int {
+  MODE_PLAIN = 0,      // new level only (forward, or adjoint without gradient)
+  MODE_SNAP_F32 = 1,   // + store the centre level u^n as an FP32 snapshot
+  MODE_SNAP_BF16 = 2,  // + BF16 snapshot with per-slab power-of-two scale
+  MODE_SNAP_F16 = 3,   // + FP16 snapshot with per-slab power-of-two scale
+  MODE_GRAD_F32 = 4,   // adjoint step + imaging condition, FP32 snapshot read
+  MODE_GRAD_BF16 = 5,
+  MODE_GRAD_F16 = 6,
+  MODE_COUNT = 7
+};
+
+__host__ __device__ constexpr bool mode_is_snap(int m) { return m >= MODE_SNAP_F32 && m <= MODE_SNAP_F16; }
+__host__ __device__ constexpr bool mode_is_grad(int m) { return m >= MODE_GRAD_F32; }
+// snapshot element format: 0 = f32, 1 = bf16, 2 = f16
+__host__ __device__ constexpr int mode_snap_fmt(int m) {
+  return m == MODE_SNAP_BF16 || m == MODE_GRAD_BF16 ? 1 : (m == MODE_SNAP_F16 || m == MODE_GRAD_F16 ? 2 : 0);
+}
+
+// Snapshot slab for 16-bit storage: 64 points along x by 2 points along axis 1
+// of one plane share one power-of-two scale.
+constexpr int kSlabX = 64;
+constexpr int kSlabY = 2;
+
+// ---------------------------------------------------------------------------
+// Tile geometry of the stencil step, per stencil radius R and dimension.
+// A CTA owns BX x BY output columns (x, axis 1) and streams a chunk of planes
+// along axis 2 (3D); in 2D it owns one BX x BY tile of the single plane.
+// ---------------------------------------------------------------------------
+template <int R, int NDIM>
+struct StepTraits {
+  static constexpr int BX = 64;                   // x outputs per CTA (16 threads x 4)
+  static constexpr int BY = 16;                   // axis-1 outputs per CTA (one row per 16 threads)
+  static constexpr int HX = (R <= 4) ? 4 : 8;     // x halo, rounded to 16 bytes for TMA
+  static constexpr int RZ = (NDIM == 3) ? R : 0;  // halo along the streamed axis
+  static constexpr int PF = (NDIM == 3) ? 2 : 0;  // extra planes prefetched ahead
+  static constexpr int NSU = RZ + 1 + PF;         // ring of u^n planes (with halo)
+  static constexpr int NSP = (NDIM == 3) ? 3 : 1; // ring of per-point tiles
+  static constexpr int UW = BX + 2 * HX;          // smem row length (floats)
+  static constexpr int UH = BY + 2 * R;           // smem rows
+  static constexpr int U_BYTES = UW * UH * 4;                // bytes of one halo box
+  static constexpr int U_STRIDE = (U_BYTES + 127) / 128 * 128;  // stage spacing (128-byte aligned)
+  static constexpr int T_ELEMS = BX * BY;
+  static constexpr int NCW = 8;                   // consumer warps
+  static constexpr int NTHREADS = (NCW + 1) * 32; // + one producer warp
+};
+
+// Per-point tiles loaded with each plane (bytes), by mode.
+template <int R, int NDIM, int MODE>
+struct StepLayout {
+  using T = StepTraits<R, NDIM>;
+  static constexpr int SNAP_ELEM = mode_snap_fmt(MODE) == 0 ? 4 : 2;
+  static constexpr int PREV_OFF = 0;
+  static constexpr int CM_OFF = T::T_ELEMS * 4;
+  static constexpr int G_OFF = 2 * T::T_ELEMS * 4;
+  static constexpr int S_OFF = 3 * T::T_ELEMS * 4;
+  static constexpr int P_BYTES = mode_is_grad(MODE) ? (3 * T::T_ELEMS * 4 + T::T_ELEMS * SNAP_ELEM)
+                                                    : 2 * T::T_ELEMS * 4;
+  static_assert(P_BYTES % 128 == 0, "per-point stage must keep 128-byte alignment");
+  // 2*(NSU+NSP) mbarriers + an abort flag, padded to 128 bytes
+  static constexpr int BAR_BYTES = ((16 * (T::NSU + T::NSP) + 16 + 127) / 128) * 128;
+  static constexpr int U_OFF = BAR_BYTES;
+  static constexpr int PST_OFF = U_OFF + T::NSU * T::U_STRIDE;
+  static constexpr int SMEM = PST_OFF + T::NSP * P_BYTES + 128;  // + runtime 128-byte alignment
+};
+
+// ---------------------------------------------------------------------------
+// Launch parameters of one stencil step (one time level).
+// Field buffer: 4 wavefield slots [slot][NZ][NY][pitch] float32.
+// ---------------------------------------------------------------------------
+struct StepParams {
+  int NX, NY, NZ;          // computational points per kernel axis
+  int pitch;               // floats per row (multiple of 8)
+  int zchunk;              // planes per CTA along axis 2
+  int cur, prev;           // field slots: centre level and previous level (overwritten by the new level)
+  float* fields;           // base of the field buffer
+  long long slot_elems;    // elements per field slot (NZ*NY*pitch)
+  // stencil coefficients (1/h^2 folded in): lap = c0*u + sum_j c{x,y,z}[j-1]*(u[-j]+u[+j])
+  float c0;
+  float cx[8], cy[8], cz[8];
+  // sponge: eta = sum_axis eta_max_axis * (delta/nbl)^2 ; nbl per kernel axis (0 on a missing axis)
+  int nblx, nbly, nblz;
+  float emx, emy, emz;     // eta_max per axis divided by nbl^2 (1/ms)
+  float half_inv_dt;       // 0.5/dt
+  float inv_dt2;           // 1/dt^2
+  // snapshot store (SNAP modes): level base pointer and slab scales
+  void* snap_out;
+  float* scale_out;
+  // gradient (GRAD modes)
+  float* grad;             // [NZ][NY][pitch]
+  int snap_level;          // level coordinate in the snapshot store
+  const float* scale_in;   // slab scales of that level
+  int slabs_x, slabs_y;    // slab grid per plane
+  int* status;             // device status word
+};
+
+// Host-side launcher for one (R, NDIM, MODE); defined in step_r<R>.cu.
+struct StepMaps {
+  CUtensorMap u;   // field buffer, halo box  (4D: x, y, z, slot)
+  CUtensorMap p;   // field buffer, tile box  (4D)
+  CUtensorMap cm;  // coefficient dt^2/m, tile box (3D)
+  CUtensorMap g;   // gradient, tile box (3D)
+  CUtensorMap s;   // snapshot store, tile box (4D: x, y, z, level)
+};
+
+cudaError_t launch_step(int R, int ndim, int mode, const StepMaps& maps, const StepParams& p,
+                        dim3 grid, cudaStream_t stream);
+int step_smem_bytes(int R, int ndim, int mode);
+int step_threads();
+int step_bx();
+int step_by(int R, int ndim);
+int step_hx(int R);
+
+// ---------------------------------------------------------------------------
+// Auxiliary kernels (aux_kernels.cu)
+// ---------------------------------------------------------------------------
+struct GridDims {
+  int NX, NY, NZ, pitch;
+  int nblx, nbly, nblz;    // sponge width per kernel axis
+  int PX, PY, PZ;          // physical points per kernel axis
+};
+
+cudaError_t launch_setup_cm(const GridDims& g, const float* m_phys, float* cm, float dt2, cudaStream_t s);
+cudaError_t launch_minmax(const float* m, long long n, unsigned int* out_minmax_bits, cudaStream_t s);
+
+// sparse points: gather (receiver sampling) and CSR injection
+struct GatherSet {
+  long long n;             // points
+  const long long* base;   // linear index of corner (0,0,0)
+  const float* frac;       // [n][3] fractions (x, axis1, axis2)
+  int ndim;
+  long long sy, sz;        // linear strides of axis 1 and axis 2
+};
+struct InjectSet {
+  int n;                   // unique grid cells
+  const long long* cell;   // linear index per cell
+  const int* rowptr;       // [n+1]
+  const int* pidx;         // contributing point per entry
+  const float* w;          // weight per entry
+  float* coef;             // per cell cm/(1+k), filled by launch_inject_coef
+};
+cudaError_t launch_gather(const GatherSet& gs, const float* field, float* out_row, cudaStream_t s);
+cudaError_t launch_inject_coef(const InjectSet& is, const GridDims& g, const float* cm,
+                               const float* eta_max_over_nbl2, float half_inv_dt, cudaStream_t s);
+cudaError_t launch_inject(const InjectSet& is, const float* values_row, float* field, cudaStream_t s);
+// injection during the gradient sweep: also corrects the imaging condition at the cell
+cudaError_t launch_inject_grad(const InjectSet& is, const float* values_row, float* field, float* grad,
+                               const void* snap_level, int snap_fmt, const float* scale_level,
+                               const GridDims& g, int slabs_x, int slabs_y, float inv_dt2, cudaStream_t s);
+
+cudaError_t launch_residual(const float* d, const float* d_obs, float* r, long long n,
+                            double* partials, int nblocks, cudaStream_t s);
+cudaError_t launch_sum_partials(const double* partials, int n, double* out, cudaStream_t s);
+int residual_blocks(long long n);
+
+cudaError_t launch_fold(const GridDims& g, const float* grad_comp, float* grad_phys, cudaStream_t s);
+cudaError_t launch_snapshot_store(const GridDims& g, const float* field, void* snap, float* scale,
+                                  int fmt, int slabs_x, int slabs_y, cudaStream_t s);
+cudaError_t launch_pack_state(const GridDims& g, const float* field, float* dense, cudaStream_t s);
+cudaError_t launch_unpack_state(const GridDims& g, const float* dense, float* field, cudaStream_t s);
+cudaError_t launch_fill_zero(float* p, long long n, cudaStream_t s);
+
+}  // namespace wave

@@ -1,0 +1,387 @@
+"""ctypes binding of libwave (include/wave.h): argument marshalling only.
+
+Every entry point of the C ABI is exposed under the same name.  Array
+arguments may be NumPy arrays (host memory: the library stages them) or
+torch tensors (device memory on the context's GPU, used in place; the call is
+enqueued on torch's current stream).  Outputs are allocated like the inputs
+when not given.  There is no fallback: if ``libwave.so`` is missing or the GPU
+path fails, the call raises.
+"""
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwave.so")
+
+WAVE_OK = 0
+WAVE_ERR_INVALID_ARG = 1
+WAVE_ERR_POINT_OUTSIDE = 2
+WAVE_ERR_UNSTABLE_DT = 3
+WAVE_ERR_OUT_OF_MEMORY = 4
+WAVE_ERR_CUDA = 5
+WAVE_ERR_TIMEOUT = 6
+WAVE_ERR_NOT_SUPPORTED = 7
+
+SNAP_FULL_FP32 = 0
+SNAP_FULL_BF16 = 1
+SNAP_FULL_FP16 = 2
+SNAP_CHECKPOINT_FP32 = 3
+SNAP_CHECKPOINT_BF16 = 4
+SNAP_CHECKPOINT_FP16 = 5
+SNAP_AUTO = 6
+SNAP_MODES = {
+    "full_fp32": SNAP_FULL_FP32, "full_bf16": SNAP_FULL_BF16, "full_fp16": SNAP_FULL_FP16,
+    "checkpoint_fp32": SNAP_CHECKPOINT_FP32, "checkpoint_bf16": SNAP_CHECKPOINT_BF16,
+    "checkpoint_fp16": SNAP_CHECKPOINT_FP16, "auto": SNAP_AUTO,
+}
+
+KERNEL_STEP, KERNEL_STEP_SNAP, KERNEL_STEP_GRAD, KERNEL_SPARSE, KERNEL_OTHER = range(5)
+KERNEL_NAMES = ["step", "step_snap", "step_grad", "sparse", "other"]
+
+
+class WaveError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (status %d): %s" % (_lib_error_string(code), code, msg))
+        self.code = code
+
+
+class c_geometry(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("nbl", ctypes.c_int32), ("shape", ctypes.c_int64 * 3),
+                ("spacing", ctypes.c_double * 3), ("origin", ctypes.c_double * 3),
+                ("sponge_vref", ctypes.c_double)]
+
+
+class c_points(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("coords", ctypes.c_void_p)]
+
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "wave_context_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_size_t]),
+    "wave_context_destroy": (ctypes.c_int, [_P]),
+    "wave_context_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "wave_context_trim": (ctypes.c_int, [_P]),
+    "wave_context_set_checkpoint_interval": (ctypes.c_int, [_P, ctypes.c_int]),
+    "wave_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "wave_last_error": (ctypes.c_char_p, [_P]),
+    "wave_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, ctypes.c_int, _P]),
+    "wave_forward_ex": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, ctypes.c_int,
+                                       _P, _P, _P, _P, _P]),
+    "wave_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, ctypes.c_int, _P]),
+    "wave_gradient": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_float,
+                                     ctypes.c_int, ctypes.c_int, _P]),
+    "wave_jacobian_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_float,
+                                             ctypes.c_int, ctypes.c_int, _P]),
+    "wave_fd_weights": (ctypes.c_int, [ctypes.c_int, _P]),
+    "wave_dt_max": (ctypes.c_double, [ctypes.c_int, _P, ctypes.c_int, ctypes.c_double]),
+    "wave_ricker": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
+    "wave_context_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
+    "wave_context_kernel_stats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                                 ctypes.POINTER(ctypes.c_double)]),
+    "wave_context_reset_stats": (ctypes.c_int, [_P]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libwave.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libwave.so is not built (run `python -m paper_1608_08658_gb300.build`)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_names():
+    return sorted(_SIGS)
+
+
+def _lib_error_string(code):
+    try:
+        return lib().wave_error_string(code).decode()
+    except Exception:  # noqa: BLE001 - only used to format an error message
+        return "status"
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x):
+    """Raw pointer of a contiguous float32/float64 array (NumPy or torch)."""
+    if x is None:
+        return None
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if not (isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"]):
+        raise ValueError("array must be a C-contiguous numpy array or a torch tensor")
+    return x.ctypes.data
+
+
+def _f32(x):
+    if x is None:
+        return None
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.float32:
+            raise TypeError("tensor must be float32")
+        return x.contiguous()
+    return np.ascontiguousarray(x, dtype=np.float32)
+
+
+def _empty_like_kind(ref, shape):
+    if ref is not None and _is_torch(ref):
+        import torch
+        return torch.empty(shape, dtype=torch.float32, device=ref.device)
+    return np.empty(shape, dtype=np.float32)
+
+
+def _stream_for(*arrays):
+    for a in arrays:
+        if a is not None and _is_torch(a) and a.is_cuda:
+            import torch
+            return ctypes.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
+    return None
+
+
+@dataclass
+class Geometry:
+    """Physical grid (x-first per-axis values) plus absorbing layer."""
+    shape: tuple
+    spacing: tuple
+    origin: tuple = None
+    nbl: int = 0
+    sponge_vref: float = 1.5
+    _c: object = field(default=None, repr=False, compare=False)
+
+    def __post_init__(self):
+        self.shape = tuple(int(s) for s in self.shape)
+        self.spacing = tuple(float(h) for h in self.spacing)
+        if self.origin is None:
+            self.origin = (0.0,) * len(self.shape)
+        self.origin = tuple(float(o) for o in self.origin)
+
+    @property
+    def ndim(self):
+        return len(self.shape)
+
+    @property
+    def phys_array_shape(self):
+        return self.shape[::-1]
+
+    @property
+    def comp_array_shape(self):
+        return tuple(n + 2 * self.nbl for n in self.shape)[::-1]
+
+    def to_c(self):
+        g = c_geometry()
+        g.ndim = self.ndim
+        g.nbl = int(self.nbl)
+        for d in range(3):
+            g.shape[d] = self.shape[d] if d < self.ndim else 1
+            g.spacing[d] = self.spacing[d] if d < self.ndim else 1.0
+            g.origin[d] = self.origin[d] if d < self.ndim else 0.0
+        g.sponge_vref = float(self.sponge_vref)
+        self._c = g
+        return g
+
+
+def _points(coords, ndim):
+    if coords is None:
+        return c_points(0, None), None
+    c = _f32(coords)
+    n = int(c.shape[0]) if c.ndim == 2 else int(c.size // ndim)
+    if n and (c.ndim != 2 or c.shape[1] != ndim):
+        raise ValueError("point coordinates must be (n, %d)" % ndim)
+    return c_points(n, _ptr(c) if n else None), c
+
+
+def _check(ctx, rc):
+    if rc != WAVE_OK:
+        raise WaveError(rc, lib().wave_last_error(ctx.handle).decode())
+
+
+class Context:
+    """Owns a wave_context (device workspace reused across calls)."""
+
+    def __init__(self, device=0, hbm_budget_bytes=0):
+        h = ctypes.c_void_p()
+        rc = lib().wave_context_create(ctypes.byref(h), int(device), int(hbm_budget_bytes))
+        if rc != WAVE_OK:
+            raise WaveError(rc, "wave_context_create failed on device %d" % device)
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().wave_context_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def workspace_bytes(self):
+        return int(lib().wave_context_workspace_bytes(self.handle))
+
+    def trim(self):
+        _check(self, lib().wave_context_trim(self.handle))
+
+    def set_checkpoint_interval(self, steps):
+        _check(self, lib().wave_context_set_checkpoint_interval(self.handle, int(steps)))
+
+    def set_profiling(self, enable):
+        _check(self, lib().wave_context_set_profiling(self.handle, int(bool(enable))))
+
+    def kernel_stats(self, kind=-1):
+        n = ctypes.c_int64()
+        t = ctypes.c_double()
+        _check(self, lib().wave_context_kernel_stats(self.handle, int(kind), ctypes.byref(n), ctypes.byref(t)))
+        return int(n.value), float(t.value)
+
+    def reset_stats(self):
+        _check(self, lib().wave_context_reset_stats(self.handle))
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def wave_forward(ctx, geom, m, src, q, rec, dt, nt, space_order, d_out=None, stream=None,
+                 u_init_prev=None, u_init=None, return_final=False):
+    """Receiver data [nt][n_rec] of the forward model (Listing 1).  With
+    ``return_final`` also returns (u^{nt-2}, u^{nt-1}) on the computational grid."""
+    m = _f32(m)
+    g = geom.to_c()
+    ps, src_c = _points(src, geom.ndim)
+    pr, rec_c = _points(rec, geom.ndim)
+    q = _f32(q) if ps.n else None
+    if d_out is None:
+        d_out = _empty_like_kind(m, (nt, pr.n))
+    ui_p, ui = _f32(u_init_prev), _f32(u_init)
+    fin_p = fin = None
+    if return_final:
+        fin_p = _empty_like_kind(m, geom.comp_array_shape)
+        fin = _empty_like_kind(m, geom.comp_array_shape)
+    st = stream if stream is not None else _stream_for(m, q, d_out)
+    rc = lib().wave_forward_ex(ctx.handle, ctypes.byref(g), _ptr(m), ctypes.byref(ps), _ptr(q), ctypes.byref(pr),
+                               _ptr(d_out) if pr.n else None, ctypes.c_float(dt), int(nt), int(space_order),
+                               _ptr(ui_p), _ptr(ui), _ptr(fin_p), _ptr(fin), st)
+    _check(ctx, rc)
+    return (d_out, fin_p, fin) if return_final else d_out
+
+
+def wave_adjoint(ctx, geom, m, src, rec, y, dt, nt, space_order, q_out=None, stream=None):
+    """Source-side traces F^T y [nt][n_src] (Listing 2 as the transpose)."""
+    m = _f32(m)
+    g = geom.to_c()
+    ps, src_c = _points(src, geom.ndim)
+    pr, rec_c = _points(rec, geom.ndim)
+    y = _f32(y) if pr.n else None
+    if q_out is None:
+        q_out = _empty_like_kind(m, (nt, ps.n))
+    st = stream if stream is not None else _stream_for(m, y, q_out)
+    rc = lib().wave_adjoint(ctx.handle, ctypes.byref(g), _ptr(m), ctypes.byref(ps), ctypes.byref(pr), _ptr(y),
+                            _ptr(q_out) if ps.n else None, ctypes.c_float(dt), int(nt), int(space_order), st)
+    _check(ctx, rc)
+    return q_out
+
+
+def wave_gradient(ctx, geom, m, src, q, rec, d_obs, dt, nt, space_order, snap_mode="auto",
+                  grad_out=None, return_residual=False, stream=None):
+    """(grad, phi[, residual]) of the objective of Eq. 2 by Eq. 3."""
+    mode = SNAP_MODES[snap_mode] if isinstance(snap_mode, str) else int(snap_mode)
+    m = _f32(m)
+    g = geom.to_c()
+    ps, src_c = _points(src, geom.ndim)
+    pr, rec_c = _points(rec, geom.ndim)
+    q = _f32(q) if ps.n else None
+    d_obs = _f32(d_obs) if pr.n else None
+    if grad_out is None:
+        grad_out = _empty_like_kind(m, geom.phys_array_shape)
+    resid = _empty_like_kind(m, (nt, pr.n)) if return_residual else None
+    phi = ctypes.c_double()
+    st = stream if stream is not None else _stream_for(m, q, d_obs, grad_out)
+    rc = lib().wave_gradient(ctx.handle, ctypes.byref(g), _ptr(m), ctypes.byref(ps), _ptr(q), ctypes.byref(pr),
+                             _ptr(d_obs), _ptr(grad_out), ctypes.byref(phi), _ptr(resid) if pr.n else None,
+                             int(mode), ctypes.c_float(dt), int(nt), int(space_order), st)
+    _check(ctx, rc)
+    if return_residual:
+        return grad_out, phi.value, resid
+    return grad_out, phi.value
+
+
+def wave_jacobian_adjoint(ctx, geom, m, src, q, rec, y, dt, nt, space_order, snap_mode="auto",
+                          grad_out=None, d_out=None, stream=None):
+    """J^T y for the map m -> receiver data (the residual replaced by y)."""
+    mode = SNAP_MODES[snap_mode] if isinstance(snap_mode, str) else int(snap_mode)
+    m = _f32(m)
+    g = geom.to_c()
+    ps, src_c = _points(src, geom.ndim)
+    pr, rec_c = _points(rec, geom.ndim)
+    q = _f32(q) if ps.n else None
+    y = _f32(y) if pr.n else None
+    if grad_out is None:
+        grad_out = _empty_like_kind(m, geom.phys_array_shape)
+    st = stream if stream is not None else _stream_for(m, q, y, grad_out)
+    rc = lib().wave_jacobian_adjoint(ctx.handle, ctypes.byref(g), _ptr(m), ctypes.byref(ps), _ptr(q),
+                                     ctypes.byref(pr), _ptr(y), _ptr(grad_out), _ptr(d_out) if pr.n else None,
+                                     int(mode), ctypes.c_float(dt), int(nt), int(space_order), st)
+    _check(ctx, rc)
+    return grad_out
+
+
+def wave_fd_weights(space_order):
+    w = np.zeros(space_order // 2 + 1 if space_order > 0 else 1, dtype=np.float64)
+    rc = lib().wave_fd_weights(int(space_order), w.ctypes.data)
+    if rc != WAVE_OK:
+        raise WaveError(rc, "bad space order %r" % (space_order,))
+    return w
+
+
+def wave_dt_max(spacing, space_order, v_max):
+    h = np.ascontiguousarray(spacing, dtype=np.float64)
+    v = lib().wave_dt_max(len(h), h.ctypes.data, int(space_order), float(v_max))
+    if v < 0:
+        raise WaveError(WAVE_ERR_INVALID_ARG, "bad arguments to wave_dt_max")
+    return v
+
+
+def wave_ricker(nt, dt, f0, t0=None, out=None):
+    if t0 is None:
+        t0 = 1.0 / f0
+    if out is None:
+        out = np.empty(nt, dtype=np.float32)
+    rc = lib().wave_ricker(_ptr(out), int(nt), ctypes.c_float(dt), ctypes.c_float(f0), ctypes.c_float(t0))
+    if rc != WAVE_OK:
+        raise WaveError(rc, "bad arguments to wave_ricker")
+    return out
+
+
+def wave_error_string(code):
+    return lib().wave_error_string(int(code)).decode()

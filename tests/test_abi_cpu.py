@@ -1,0 +1,80 @@
+"""CPU checks of the C ABI: the library builds and loads, exports every entry
+point declared in include/wave.h, and its host-side helpers (weights, CFL
+limit, Ricker wavelet, error strings) agree with the oracle.  No GPU compute."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1608_08658_gb300 import build as libbuild
+from paper_1608_08658_gb300 import wave
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    libbuild.build()
+    return wave.lib()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "wave.h")).read()
+    return sorted(set(re.findall(r"WAVE_API\s+[\w\s\*]+?\b(wave_\w+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    # the binding covers the same set
+    assert sorted(names) == wave.exported_names()
+
+
+@pytest.mark.parametrize("so", [2, 4, 8, 12, 16])
+def test_fd_weights_match_oracle(lib, so):
+    np.testing.assert_allclose(wave.wave_fd_weights(so), oracle.fd.fd_weights(so), rtol=2e-15, atol=1e-16)
+
+
+def test_fd_weights_reject_bad_order(lib):
+    for bad in (0, 3, 18):
+        with pytest.raises(wave.WaveError):
+            wave.wave_fd_weights(bad)
+
+
+@pytest.mark.parametrize("so,spacing,v", [(4, (10.0, 10.0), 1.5), (8, (10.0, 10.0, 10.0), 2.5),
+                                          (16, (12.5, 7.0, 9.0), 4.5)])
+def test_dt_max_matches_oracle(lib, so, spacing, v):
+    assert abs(wave.wave_dt_max(spacing, so, v) - oracle.model.dt_max(so, spacing, v)) < 1e-12
+
+
+def test_ricker_matches_oracle(lib):
+    nt, dt, f0 = 700, 1.633, 0.01
+    r = wave.wave_ricker(nt, dt, f0)
+    ref = oracle.model.ricker(nt, np.float32(dt), np.float32(f0), t0=np.float32(1.0 / f0))
+    np.testing.assert_allclose(r, ref, rtol=0, atol=2e-7)
+
+
+def test_error_strings(lib):
+    for code in range(8):
+        assert wave.wave_error_string(code)
+    assert "unknown" in wave.wave_error_string(99)
+
+
+def test_context_without_gpu_reports_error(lib):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    h = ctypes.c_void_p()
+    rc = lib.wave_context_create(ctypes.byref(h), 0, 0)
+    assert rc in (wave.WAVE_ERR_CUDA, wave.WAVE_ERR_NOT_SUPPORTED)
+    assert not h.value
+    assert lib.wave_context_destroy(None) == 0

@@ -1,0 +1,184 @@
+"""GPU parity of the CUDA path against the FP64 oracle (through the C ABI).
+
+Tolerances: receiver data and adjoint traces rel-L2 <= 1e-4, gradient rel-L2
+<= 5e-4 (FP32 stencil, FP64 oracle); single steps elementwise within 1e-5 of
+the local field scale.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_cases import config1, geometries, rel_l2, small2d, small3d
+
+torch = pytest.importorskip("torch")
+from paper_1608_08658_gb300 import wave  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    c = wave.Context(0)
+    yield c
+    c.close()
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def test_forward_2d_101x101_order4(ctx):
+    og, m, dt, nt, so, src, q, rec = config1()
+    _, geom = geometries(og)
+    d = wave.wave_forward(ctx, geom, _dev(m), src, _dev(q), rec, dt, nt, so).cpu().numpy()
+    ref = oracle.wave.forward(og, m, dt, nt, so, q, src, rec).d
+    err = rel_l2(d, ref)
+    print("2D 101x101 so4 nt500: rel-L2 receivers %.3e" % err)
+    assert err <= 1e-4
+
+
+@pytest.mark.parametrize("so", [2, 4, 6, 8, 10, 12, 14, 16])
+def test_forward_3d_all_orders(ctx, so):
+    og, m, dt, nt, so, src, q, rec = small3d(so)
+    _, geom = geometries(og)
+    d, fp, fl = wave.wave_forward(ctx, geom, _dev(m), src, _dev(q), rec, dt, nt, so, return_final=True)
+    ref = oracle.wave.forward(og, m, dt, nt, so, q, src, rec)
+    e_d = rel_l2(d.cpu().numpy(), ref.d)
+    e_u = np.abs(fl.cpu().numpy() - ref.u_last).max() / np.abs(ref.u_last).max()
+    print("3D so%d: rel-L2 receivers %.3e, max field err %.3e" % (so, e_d, e_u))
+    assert e_d <= 1e-4 and e_u <= 1e-4
+
+
+@pytest.mark.parametrize("so", [2, 4, 8, 12, 16])
+def test_forward_2d_all_orders(ctx, so):
+    og, m, dt, nt, so, src, q, rec = small2d(so)
+    _, geom = geometries(og)
+    d = wave.wave_forward(ctx, geom, _dev(m), src, _dev(q), rec, dt, nt, so).cpu().numpy()
+    ref = oracle.wave.forward(og, m, dt, nt, so, q, src, rec).d
+    assert rel_l2(d, ref) <= 1e-4
+
+
+@pytest.mark.parametrize("so,ndim", [(2, 3), (8, 3), (16, 3), (4, 2), (14, 2)])
+def test_single_step_from_random_state(ctx, so, ndim):
+    og, m, dt, _, so, src, _, rec = small3d(so, nt=2) if ndim == 3 else small2d(so, nt=2)
+    _, geom = geometries(og)
+    r = np.random.default_rng(77)
+    u0 = r.standard_normal(og.array_shape).astype(np.float32)
+    u1 = r.standard_normal(og.array_shape).astype(np.float32)
+    q = r.standard_normal((3, len(src))).astype(np.float32)
+    d, fp, fl = wave.wave_forward(ctx, geom, _dev(m), src, _dev(q), rec, dt, 3, so, u_init_prev=_dev(u0),
+                                  u_init=_dev(u1), return_final=True)
+    mc = oracle.model.pad_model(og, m)
+    eta = oracle.model.damping(og)
+    Ps, Pr = oracle.wave.operators(og, src, rec)
+    ref = oracle.wave.forward_op(mc, eta, og.spacing, dt, 3, so, q, Ps, Pr, u_init_prev=u0, u_init=u1)
+    scale = np.abs(ref.u_last).max()
+    assert np.abs(fp.cpu().numpy() - ref.u_prev).max() <= 1e-5 * np.abs(ref.u_prev).max()
+    assert np.abs(fl.cpu().numpy() - ref.u_last).max() <= 1e-5 * scale
+    assert rel_l2(d.cpu().numpy(), ref.d) <= 1e-5
+
+
+@pytest.mark.parametrize("case", ["3d8", "2d4"])
+def test_adjoint_and_dot_product(ctx, case):
+    og, m, dt, nt, so, src, q, rec = small3d(8) if case == "3d8" else small2d(4)
+    _, geom = geometries(og)
+    r = np.random.default_rng(5)
+    y = r.standard_normal((nt, len(rec))).astype(np.float32)
+    qa = wave.wave_adjoint(ctx, geom, _dev(m), src, rec, _dev(y), dt, nt, so).cpu().numpy()
+    ref = oracle.wave.adjoint(og, m, dt, nt, so, y, src, rec)
+    assert rel_l2(qa, ref) <= 1e-4
+    # dot test of Eq. 5-6 on the GPU operators (FP32 stencil, FP64 sums)
+    d = wave.wave_forward(ctx, geom, _dev(m), src, _dev(q), rec, dt, nt, so).cpu().numpy()
+    lhs = np.sum(d.astype(np.float64) * y)
+    rhs = np.sum(q.astype(np.float64) * qa)
+    print("%s dot test: <Fq,y> = %.9e, <q,F^T y> = %.9e, rel %.2e" % (case, lhs, rhs, abs(lhs - rhs) / abs(lhs)))
+    assert abs(lhs - rhs) <= 1e-4 * max(abs(lhs), abs(rhs))
+
+
+@pytest.mark.parametrize("case", ["3d8", "2d4", "3d16"])
+def test_gradient_full_fp32(ctx, case):
+    so = {"3d8": 8, "2d4": 4, "3d16": 16}[case]
+    og, m, dt, nt, so, src, q, rec = small3d(so) if case.startswith("3d") else small2d(so)
+    _, geom = geometries(og)
+    r = np.random.default_rng(9)
+    d_obs = (oracle.wave.forward(og, m * 1.02, dt, nt, so, q, src, rec).d).astype(np.float32)
+    g, phi = wave.wave_gradient(ctx, geom, _dev(m), src, _dev(q), rec, _dev(d_obs), dt, nt, so,
+                                snap_mode="full_fp32")
+    g_ref, phi_ref = oracle.wave.gradient(og, m, dt, nt, so, q, src, rec, d_obs)
+    e_g = rel_l2(g.cpu().numpy(), g_ref)
+    e_phi = abs(phi - phi_ref) / phi_ref
+    print("%s gradient: rel-L2 %.3e, objective rel %.3e" % (case, e_g, e_phi))
+    assert e_g <= 5e-4 and e_phi <= 1e-4
+    del r
+
+
+def test_gradient_storage_modes(ctx):
+    og, m, dt, nt, so, src, q, rec = small3d(8, nt=70)
+    _, geom = geometries(og)
+    d_obs = (oracle.wave.forward(og, m * 0.98, dt, nt, so, q, src, rec).d).astype(np.float32)
+    g_ref, _ = oracle.wave.gradient(og, m, dt, nt, so, q, src, rec, d_obs)
+    res = {}
+    for mode in ["full_fp32", "checkpoint_fp32", "full_bf16", "full_fp16", "checkpoint_fp16", "checkpoint_bf16"]:
+        ctx.set_checkpoint_interval(16)
+        g, phi = wave.wave_gradient(ctx, geom, _dev(m), src, _dev(q), rec, _dev(d_obs), dt, nt, so, snap_mode=mode)
+        res[mode] = (g.cpu().numpy(), phi)
+    ctx.set_checkpoint_interval(0)
+    # checkpointed recomputation reproduces the stored forward bit for bit
+    np.testing.assert_array_equal(res["checkpoint_fp32"][0], res["full_fp32"][0])
+    np.testing.assert_array_equal(res["checkpoint_fp16"][0], res["full_fp16"][0])
+    np.testing.assert_array_equal(res["checkpoint_bf16"][0], res["full_bf16"][0])
+    for mode, (g, _) in res.items():
+        print("gradient %s: rel-L2 vs oracle %.3e" % (mode, rel_l2(g, g_ref)))
+    assert rel_l2(res["full_fp32"][0], g_ref) <= 5e-4
+    assert rel_l2(res["full_fp16"][0], g_ref) <= 5e-4
+    assert rel_l2(res["full_bf16"][0], g_ref) <= 1e-2
+
+
+def test_jacobian_adjoint_matches_gradient(ctx):
+    og, m, dt, nt, so, src, q, rec = small2d(6)
+    _, geom = geometries(og)
+    r = np.random.default_rng(4)
+    y = r.standard_normal((nt, len(rec))).astype(np.float32)
+    gj = wave.wave_jacobian_adjoint(ctx, geom, _dev(m), src, _dev(q), rec, _dev(y), dt, nt, so,
+                                    snap_mode="full_fp32").cpu().numpy()
+    # J^T y equals the gradient for observed data d_pred - y (oracle)
+    d_pred = oracle.wave.forward(og, m, dt, nt, so, q, src, rec).d
+    g_ref, _ = oracle.wave.gradient(og, m, dt, nt, so, q, src, rec, d_pred - y)
+    assert rel_l2(gj, g_ref) <= 5e-4
+
+
+def test_host_buffers_match_device_buffers(ctx):
+    og, m, dt, nt, so, src, q, rec = small2d(8)
+    _, geom = geometries(og)
+    d_host = wave.wave_forward(ctx, geom, m, src, q, rec, dt, nt, so)
+    d_dev = wave.wave_forward(ctx, geom, _dev(m), _dev(src), _dev(q), _dev(rec), dt, nt, so).cpu().numpy()
+    np.testing.assert_array_equal(d_host, d_dev)
+
+
+def test_errors_are_reported(ctx):
+    og, m, dt, nt, so, src, q, rec = small2d(4)
+    _, geom = geometries(og)
+    bad = rec.copy()
+    bad[3, 0] = -50.0
+    with pytest.raises(wave.WaveError) as e:
+        wave.wave_forward(ctx, geom, m, src, q, bad, dt, nt, so)
+    assert e.value.code == wave.WAVE_ERR_POINT_OUTSIDE
+    with pytest.raises(wave.WaveError) as e:
+        wave.wave_forward(ctx, geom, m, src, q, rec, dt * 3.0, nt, so)
+    assert e.value.code == wave.WAVE_ERR_UNSTABLE_DT
+    with pytest.raises(wave.WaveError) as e:
+        wave.wave_forward(ctx, geom, m, src, q, rec, dt, nt, 5)
+    assert e.value.code == wave.WAVE_ERR_INVALID_ARG
+    with pytest.raises(wave.WaveError) as e:
+        wave.wave_forward(ctx, geom, -m, src, q, rec, dt, nt, so)
+    assert e.value.code == wave.WAVE_ERR_INVALID_ARG
+    with wave.Context(0, hbm_budget_bytes=1 << 20) as small:
+        with pytest.raises(wave.WaveError) as e:
+            wave.wave_forward(small, geom, m, src, q, rec, dt, nt, so)
+        assert e.value.code == wave.WAVE_ERR_OUT_OF_MEMORY
+    # the context still works after errors
+    d = wave.wave_forward(ctx, geom, m, src, q, rec, dt, nt, so)
+    assert np.isfinite(d).all()

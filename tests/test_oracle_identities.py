@@ -193,3 +193,17 @@ def test_sponge_profile_shape_and_absorption():
     e_damped = np.sum(wave.forward_op(m, eta, geom.spacing, dt, nt, so, q, Ps, empty).u_last[inner] ** 2)
     e_free = np.sum(wave.forward_op(m, 0 * eta, geom.spacing, dt, nt, so, q, Ps, empty).u_last[inner] ** 2)
     assert e_damped < 1e-2 * e_free, (e_damped, e_free)
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_windowed_model_and_damping_equal_crops(ndim):
+    geom = _geom(ndim, nbl=3)
+    rng = np.random.default_rng(12)
+    m = rng.uniform(0.1, 0.4, size=geom.phys_array_shape)
+    full_m = model.pad_model(geom, m)
+    full_e = model.damping(geom)
+    win = [(0, 4), (2, 9), (1, 7)][:ndim]
+    win = [(a, min(b, n)) for (a, b), n in zip(win, geom.array_shape)]
+    sl = tuple(slice(a, b) for a, b in win)
+    np.testing.assert_array_equal(model.pad_model(geom, m, window=win), full_m[sl])
+    np.testing.assert_array_equal(model.damping(geom, window=win), full_e[sl])
