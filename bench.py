@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark of the wave library's hot path on one or more GPUs.
+
+One step = one FWI gradient evaluation through the C ABI (wave_gradient):
+forward modelling with receiver sampling and source injection, residual and
+FP64 objective, adjoint sweep with the fused imaging condition, padding fold
+(checkpointed recomputation supplies the forward wavefield).  Workload: the 3D
+throughput configuration -- 512^3 physical grid, h = 10 m, 40-point sponge
+(592^3 computational points), two-layer velocity 1.5/2.5 km/s times a seeded
+5% Gaussian perturbation of 50 m correlation length, space order 8, nt = 1000,
+one 15 Hz Ricker source at the surface centre, 512 x 512 receivers on the
+surface nodes at 20 m depth.  Observed data come from the perturbed model; the
+gradient is evaluated at the unperturbed two-layer model.
+
+Throughput = point updates (forward + adjoint: 2 * points * (nt-1)) / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpts/s & % HBM roofline (3D SO8 fwd/grad); shots/s & p50/p99 latency served"
+FALLBACK_HBM_GBS = 6800.0
+
+# algorithmic bytes per computational point and launch, by kernel kind
+#   step: read u^n, u^{n-1}, cm, write u^{n+1}                    16 B
+#   step_snap: + snapshot write (4 B FP32, 2 B 16-bit)
+#   step_grad: + snapshot read, gradient read + write (8 B)
+BYTES_PER_POINT = {"step": 16, "step_snap_fp32": 20, "step_snap_16": 18, "step_grad_fp32": 28, "step_grad_16": 26}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=512, help="physical points per axis")
+    ap.add_argument("--nt", type=int, default=1000)
+    ap.add_argument("--so", type=int, default=8)
+    ap.add_argument("--nbl", type=int, default=40)
+    ap.add_argument("--snap", default="checkpoint_fp32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-nz", type=int, default=8, help="physical depth points of the CPU sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_workload(n, nbl, so, nt):
+    from paper_1608_08658_gb300 import inputs
+    shape = (n, n, n)
+    h = (10.0, 10.0, 10.0)
+    v0 = inputs.two_layer_random_velocity(shape, h, 1.5, 2.5, sigma=0.0)
+    v_true = inputs.two_layer_random_velocity(shape, h, 1.5, 2.5, sigma=0.05, corr_len=50.0, seed=7)
+    ext = (n - 1) * h[0]
+    src = np.array([[0.5 * ext, 0.5 * ext, 20.0]], dtype=np.float32)
+    rec = inputs.surface_grid_receivers(n, n, (h[0], h[1]), 20.0)
+    return dict(shape=shape, spacing=h, nbl=nbl, so=so, nt=nt, v0=v0, v_true=v_true, src=src, rec=rec,
+                vmax=float(v_true.max()), f0=0.015)
+
+
+def workload_config(w, snap):
+    n = w["shape"][0]
+    ncomp = n + 2 * w["nbl"]
+    return {
+        "workload": "3D FWI gradient %d^3 (+%d sponge = %d^3), h=10 m, so=%d, nt=%d, two-layer 1.5/2.5 km/s + 5%% "
+                    "perturbation, 1 Ricker 15 Hz, %dx%d surface receivers" % (n, w["nbl"], ncomp, w["so"], w["nt"],
+                                                                              n, n),
+        "grid": list(w["shape"]), "nbl": w["nbl"], "space_order": w["so"], "nt": w["nt"], "snap_mode": snap,
+        "points_per_step": "2 * %d^3 * (nt-1) (forward + adjoint updates)" % ncomp,
+        "l2": "inputs larger than L2 (each wavefield %.2f GB)" % (ncomp ** 3 * 4 / 1e9),
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=None):
+        self.rows = []
+        self.proc = None
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_index is not None:
+            cmd += ["-i", str(gpu_index)]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        pw = [num(r[3]) for r in self.rows if num(r[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(self.rows), "reasons": reasons}
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (reported baseline)
+# ---------------------------------------------------------------------------
+
+def cpu_sample(w, nz_phys, steps_nt=3):
+    """Oracle gradient on a bounded sample: full x-y extent, nz_phys physical
+    depth points, the same sponge, spacing, order; nt = steps_nt."""
+    import oracle
+    n = w["shape"][0]
+    og = oracle.model.Geometry(shape=(n, n, nz_phys), spacing=w["spacing"], nbl=w["nbl"], sponge_vref=w["vmax"])
+    m = (1.0 / w["v0"][:nz_phys] ** 2).astype(np.float32)
+    dt = 0.4 * oracle.model.dt_max(w["so"], og.spacing, w["vmax"])
+    q = oracle.model.ricker(steps_nt, dt, w["f0"])[:, None]
+    src = w["src"].copy()
+    src[:, 2] = 20.0
+    rec = w["rec"][:: max(1, len(w["rec"]) // 4096)].copy()
+    d_obs = np.zeros((steps_nt, len(rec)))
+    pts = int(np.prod(og.comp_shape))
+
+    def run():
+        t0 = time.perf_counter()
+        oracle.wave.gradient(og, m, dt, steps_nt, w["so"], q, src, rec, d_obs)
+        return time.perf_counter() - t0
+    return run, pts, steps_nt, og
+
+
+def cpu_baseline(w, nz):
+    run, pts, nt, og = cpu_sample(w, nz)
+    t = run()
+    units = 2.0 * pts * (nt - 1)
+    return {"value": units / t / 1e9, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
+            "sample": "FP64 NumPy oracle gradient on %dx%dx%d computational points (%d physical depth points + sponge),"
+                      " nt=%d (2*%d point updates), %.1f s, single thread" % (og.comp_shape + (nz, nt, nt - 1, t))}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    w = make_workload(args.n, args.nbl, args.so, args.nt)
+    run, pts, nt, og = cpu_sample(w, args.cpu_sample_nz)
+    for _ in range(args.warmup):
+        run()
+    ts = [run() for _ in range(args.steps)]
+    t = float(np.mean(ts))
+    v = 2.0 * pts * (nt - 1) / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Gpts/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w, "full history (oracle)"),
+            "cpu_baseline": {"value": v, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step: FP64 oracle gradient on %dx%dx%d computational points, nt=%d"
+                                       % (og.comp_shape + (nt,))},
+            "e2e": {"value": v, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1608_08658_gb300 import wave
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = make_workload(args.n, args.nbl, args.so, args.nt)
+    so, nt = args.so, args.nt
+    geom = wave.Geometry(shape=w["shape"], spacing=w["spacing"], nbl=w["nbl"], sponge_vref=w["vmax"])
+    dt = 0.4 * wave.wave_dt_max(w["spacing"], so, w["vmax"])
+    q = wave.wave_ricker(nt, dt, w["f0"]).reshape(nt, 1)
+    m0 = (1.0 / w["v0"] ** 2).astype(np.float32)
+    mt = (1.0 / w["v_true"] ** 2).astype(np.float32)
+    ctx = wave.Context(local_rank)
+    stream = torch.cuda.current_stream(dev)
+    m0_d = torch.from_numpy(m0).to(dev)
+    q_d = torch.from_numpy(q).to(dev)
+    src_d = torch.from_numpy(w["src"]).to(dev)
+    rec_d = torch.from_numpy(w["rec"]).to(dev)
+    dobs_d = wave.wave_forward(ctx, geom, torch.from_numpy(mt).to(dev), src_d, q_d, rec_d, dt, nt, so)
+    grad_d = torch.empty_like(m0_d)
+
+    def step():
+        return wave.wave_gradient(ctx, geom, m0_d, src_d, q_d, rec_d, dobs_d, dt, nt, so, snap_mode=args.snap,
+                                  grad_out=grad_d)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ctx.reset_stats()
+    ctx.set_profiling(True)
+    clocks = ClockSampler(local_rank if world > 1 else None) if rank == 0 else None
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    phi = None
+    for _ in range(args.steps):
+        _, phi = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    clk = clocks.stop() if clocks else None
+    ctx.set_profiling(False)
+    stats = {wave.KERNEL_NAMES[k]: ctx.kernel_stats(k) for k in range(5)}
+    launches = ctx.kernel_stats(-1)[0]
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    npts = int(np.prod([s + 2 * w["nbl"] for s in w["shape"]]))
+    units = 2.0 * npts * (nt - 1)
+    value = world * units / (ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel kind
+    fmt16 = "bf16" in args.snap or "fp16" in args.snap
+    bpp = {"step": BYTES_PER_POINT["step"],
+           "step_snap": BYTES_PER_POINT["step_snap_16" if fmt16 else "step_snap_fp32"],
+           "step_grad": BYTES_PER_POINT["step_grad_16" if fmt16 else "step_grad_fp32"]}
+    peak, peak_kind = hbm_peak()
+    kernels = {}
+    for k in ("step", "step_snap", "step_grad"):
+        n, tms = stats[k]
+        if n:
+            avg = tms / n
+            kernels[k] = {"launches": n, "avg_ms": avg, "share": tms / max(1e-9, sum(v[1] for v in stats.values())),
+                          "bytes_per_point": bpp[k], "achieved_gbs": bpp[k] * npts / (avg * 1e-3) / 1e9}
+    dom = max(kernels, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["launches"])
+    ach = kernels[dom]["achieved_gbs"]
+    roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "kernel": dom, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs copy test)"
+                if peak_kind == "measured" else "fallback 6.8 TB/s", "bytes_per_point": bpp[dom],
+                "points_per_launch": npts}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        m_h, q_h, src_h, rec_h = pin(m0), pin(q), pin(w["src"]), pin(w["rec"])
+        dobs_h = dobs_d.cpu().pin_memory().numpy()
+        g_h = torch.empty(m0.shape, dtype=torch.float32).pin_memory().numpy()
+
+        def step_host():
+            return wave.wave_gradient(ctx, geom, m_h, src_h, q_h, rec_h, dobs_h, dt, nt, so, snap_mode=args.snap,
+                                      grad_out=g_h, stream=ctypes_stream(stream))
+        step_host()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_host()
+        torch.cuda.synchronize()
+        te = (time.perf_counter() - t0) / args.steps
+        if dist:
+            t = torch.tensor([te], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        h2d = m_h.nbytes + q_h.nbytes + dobs_h.nbytes + src_h.nbytes + rec_h.nbytes
+        e2e = {"value": world * units / te / 1e9, "unit": "Gpts/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(g_h.nbytes + 8), "ms_per_step": te * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_sample_nz)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(w, args.snap),
+                "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(launches), "clocks": clk, "objective": phi}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def ctypes_stream(stream):
+    import ctypes
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.gpus != world and world > 1:
+        print("warning: --gpus %d but WORLD_SIZE %d" % (args.gpus, world), file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -175,7 +175,7 @@ def test_errors_are_reported(ctx):
     with pytest.raises(wave.WaveError) as e:
         wave.wave_forward(ctx, geom, -m, src, q, rec, dt, nt, so)
     assert e.value.code == wave.WAVE_ERR_INVALID_ARG
-    with wave.Context(0, hbm_budget_bytes=1 << 20) as small:
+    with wave.Context(0, hbm_budget_bytes=64 << 10) as small:
         with pytest.raises(wave.WaveError) as e:
             wave.wave_forward(small, geom, m, src, q, rec, dt, nt, so)
         assert e.value.code == wave.WAVE_ERR_OUT_OF_MEMORY
