@@ -51,6 +51,8 @@ def parse_args():
     ap.add_argument("--so", type=int, default=8)
     ap.add_argument("--nbl", type=int, default=40)
     ap.add_argument("--snap", default="checkpoint_fp32")
+    ap.add_argument("--mode", default="gradient", choices=["gradient", "forward"],
+                    help="gradient: one FWI gradient per step (default); forward: one forward modelling per step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-nz", type=int, default=8, help="physical depth points of the CPU sample")
@@ -74,15 +76,17 @@ def make_workload(n, nbl, so, nt):
                 vmax=float(v_true.max()), f0=0.015)
 
 
-def workload_config(w, snap):
+def workload_config(w, snap, mode="gradient"):
     n = w["shape"][0]
     ncomp = n + 2 * w["nbl"]
+    what = "FWI gradient" if mode == "gradient" else "forward modelling"
     return {
-        "workload": "3D FWI gradient %d^3 (+%d sponge = %d^3), h=10 m, so=%d, nt=%d, two-layer 1.5/2.5 km/s + 5%% "
+        "workload": "3D " + what + " %d^3 (+%d sponge = %d^3), h=10 m, so=%d, nt=%d, two-layer 1.5/2.5 km/s + 5%% "
                     "perturbation, 1 Ricker 15 Hz, %dx%d surface receivers" % (n, w["nbl"], ncomp, w["so"], w["nt"],
                                                                               n, n),
         "grid": list(w["shape"]), "nbl": w["nbl"], "space_order": w["so"], "nt": w["nt"], "snap_mode": snap,
-        "points_per_step": "2 * %d^3 * (nt-1) (forward + adjoint updates)" % ncomp,
+        "points_per_step": ("2 * %d^3 * (nt-1) (forward + adjoint updates)" % ncomp) if mode == "gradient"
+        else ("%d^3 * (nt-1)" % ncomp),
         "l2": "inputs larger than L2 (each wavefield %.2f GB)" % (ncomp ** 3 * 4 / 1e9),
     }
 
@@ -138,6 +142,30 @@ class ClockSampler:
         reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower().startswith("active")})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "power_w_max": max(pw) if pw else None, "samples": len(self.rows), "reasons": reasons}
+
+
+KERNEL_SOURCES = ("step_kernel.cuh", "ptx.cuh", "wave_internal.h")
+TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "step_kernel_r4_3d_336cube.md")
+
+
+def measured_traffic(kind, points):
+    """DRAM bytes per launch from the committed ncu summary, scaled to `points`;
+    None when the kernel sources changed since the counters were taken."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1608_08658_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    digest = h.hexdigest()[:16]
+    try:
+        with open(TRAFFIC_TABLE) as fh:
+            for line in fh:
+                cells = [c.strip() for c in line.strip().strip("|").split("|")]
+                if len(cells) == 3 and cells[0] == kind and cells[2] == digest:
+                    return float(cells[1]) * points
+    except OSError:
+        pass
+    return None
 
 
 def hbm_peak():
@@ -202,6 +230,7 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(w, "full history (oracle)"),
+            # the oracle sample is a gradient (forward + adjoint point updates)
             "cpu_baseline": {"value": v, "unit": "Gpts/s", "cores": 1, "kind": "oracle",
                              "sample": "each step: FP64 oracle gradient on %dx%dx%d computational points, nt=%d"
                                        % (og.comp_shape + (nt,))},
@@ -237,10 +266,14 @@ def run_ours(args, rank, world, local_rank):
     q_d = torch.from_numpy(q).to(dev)
     src_d = torch.from_numpy(w["src"]).to(dev)
     rec_d = torch.from_numpy(w["rec"]).to(dev)
-    dobs_d = wave.wave_forward(ctx, geom, torch.from_numpy(mt).to(dev), src_d, q_d, rec_d, dt, nt, so)
+    mt_d = torch.from_numpy(mt).to(dev)
+    dobs_d = wave.wave_forward(ctx, geom, mt_d, src_d, q_d, rec_d, dt, nt, so)
     grad_d = torch.empty_like(m0_d)
 
     def step():
+        if args.mode == "forward":
+            wave.wave_forward(ctx, geom, mt_d, src_d, q_d, rec_d, dt, nt, so, d_out=dobs_d)
+            return None, None
         return wave.wave_gradient(ctx, geom, m0_d, src_d, q_d, rec_d, dobs_d, dt, nt, so, snap_mode=args.snap,
                                   grad_out=grad_d)
 
@@ -271,7 +304,8 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     npts = int(np.prod([s + 2 * w["nbl"] for s in w["shape"]]))
-    units = 2.0 * npts * (nt - 1)
+    sweeps = 1 if args.mode == "forward" else 2
+    units = sweeps * npts * (nt - 1)
     value = world * units / (ms * 1e-3) / 1e9
 
     # roofline of the dominant kernel kind
@@ -290,7 +324,7 @@ def run_ours(args, rank, world, local_rank):
     dom = max(kernels, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["launches"])
     ach = kernels[dom]["achieved_gbs"]
     roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": None, "kernel": dom, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs copy test)"
+                "traffic": measured_traffic(dom, npts) if args.so == 8 and not fmt16 else None, "kernel": dom, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs copy test)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s", "bytes_per_point": bpp[dom],
                 "points_per_launch": npts}
 
@@ -298,11 +332,16 @@ def run_ours(args, rank, world, local_rank):
     e2e = None
     if not args.no_e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
-        m_h, q_h, src_h, rec_h = pin(m0), pin(q), pin(w["src"]), pin(w["rec"])
+        m_h, q_h, src_h, rec_h = pin(mt if args.mode == "forward" else m0), pin(q), pin(w["src"]), pin(w["rec"])
         dobs_h = dobs_d.cpu().pin_memory().numpy()
         g_h = torch.empty(m0.shape, dtype=torch.float32).pin_memory().numpy()
 
+        d_h = torch.empty(tuple(dobs_d.shape), dtype=torch.float32).pin_memory().numpy()
+
         def step_host():
+            if args.mode == "forward":
+                return wave.wave_forward(ctx, geom, m_h, src_h, q_h, rec_h, dt, nt, so, d_out=d_h,
+                                         stream=ctypes_stream(stream))
             return wave.wave_gradient(ctx, geom, m_h, src_h, q_h, rec_h, dobs_h, dt, nt, so, snap_mode=args.snap,
                                       grad_out=g_h, stream=ctypes_stream(stream))
         step_host()
@@ -318,9 +357,14 @@ def run_ours(args, rank, world, local_rank):
             t = torch.tensor([te], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             te = float(t.item())
-        h2d = m_h.nbytes + q_h.nbytes + dobs_h.nbytes + src_h.nbytes + rec_h.nbytes
+        if args.mode == "forward":
+            h2d = m_h.nbytes + q_h.nbytes + src_h.nbytes + rec_h.nbytes
+            d2h = d_h.nbytes
+        else:
+            h2d = m_h.nbytes + q_h.nbytes + dobs_h.nbytes + src_h.nbytes + rec_h.nbytes
+            d2h = g_h.nbytes + 8
         e2e = {"value": world * units / te / 1e9, "unit": "Gpts/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(g_h.nbytes + 8), "ms_per_step": te * 1e3}
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": te * 1e3}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -329,7 +373,8 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(w, args.snap),
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(w, args.snap if args.mode == "gradient" else None, args.mode),
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "objective": phi}
         print(json.dumps(line), flush=True)

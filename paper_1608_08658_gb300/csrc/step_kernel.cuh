@@ -25,6 +25,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+
 #include "ptx.cuh"
 #include "wave_internal.h"
 
@@ -86,8 +87,16 @@ __device__ __forceinline__ float4 load_snap4_smem(const unsigned char* p, float 
   return make_float4(a.x * s, a.y * s, b.x * s, b.y * s);
 }
 
+// Resident CTAs per SM requested from the register allocator: 3 up to radius
+// 4 (72 registers), 2 for radius 5-6 (<= 113 registers); radius 7-8 are held
+// to one CTA per SM by their shared-memory ring anyway.
+#ifndef WAVE_STEP_MINB
+#define WAVE_STEP_MINB 3
+#endif
+
+
 template <int R, int NDIM, int MODE>
-__global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS)
+__global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_STEP_MINB : (R <= 6 ? 2 : 1)))
     step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
                 const __grid_constant__ CUtensorMap tm_cm, const __grid_constant__ CUtensorMap tm_g,
                 const __grid_constant__ CUtensorMap tm_s, const StepParams p) {
@@ -197,16 +206,34 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS)
   const int gy = y0 + ty;
   const bool store_ok = (gx < p.NX) && (gy < p.NY);
   const int lofs = (R + ty) * T::UW + T::HX + 4 * tx;  // centre of this quad in a U stage
+  const int tofs = (ty * T::BX + 4 * tx) * 4;          // byte offset of this quad in a tile
 
   // sponge along x (per point) and axis 1 (per row)
-  float ex[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) ex[i] = sponge_term(gx + i, p.NX, p.nblx, p.emx);
   const float ey = sponge_term(gy, p.NY, p.nbly, p.emy);
-
-  float4 q[2 * RZ + 1];
+  float exy[4];
 #pragma unroll
-  for (int i = 0; i < 2 * RZ + 1; ++i) q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int i = 0; i < 4; ++i) exy[i] = sponge_term(gx + i, p.NX, p.nblx, p.emx) + ey;
+  // all terms are >= 0: the column is undamped iff the largest is zero
+  const float exy_max = fmaxf(fmaxf(exy[0], exy[1]), fmaxf(exy[2], exy[3]));
+
+  // coefficients as packed pairs (loop invariant)
+  const float2 c0v = make_float2(p.c0, p.c0);
+  float2 cxv[R], cyv[R], czv[RZ > 0 ? RZ : 1];
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    cxv[k] = make_float2(p.cx[k], p.cx[k]);
+    cyv[k] = make_float2(p.cy[k], p.cy[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < RZ; ++k) czv[k] = make_float2(p.cz[k], p.cz[k]);
+
+  // Register queue of the centre level along the streamed axis: before output
+  // plane z, q[0 .. 2RZ-1] hold planes z-RZ .. z+RZ-1; plane z+RZ lands in
+  // q[2RZ] and the queue moves down by one afterwards.
+  constexpr int NQ = 2 * RZ + 1;
+  float4 q[NQ];
+#pragma unroll
+  for (int i = 0; i < NQ; ++i) q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
   bool ok = true;
 #pragma unroll
@@ -215,7 +242,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS)
     ok = mbar_wait_bounded(&fullU[slot], (s / T::NSU) & 1, abort_flag, kWaitLimitNs);
     ok = __all_sync(0xffffffffu, ok);
     if (!ok) break;
-    q[s + 1] = lds4(Ubase + slot * (T::U_STRIDE / 4) + lofs);
+    q[s] = lds4(Ubase + slot * (T::U_STRIDE / 4) + lofs);
     if (s < RZ) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&emptyU[slot]);
@@ -223,31 +250,44 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS)
   }
 
   const long long plane_elems = static_cast<long long>(p.NY) * p.pitch;
-  for (int j = 0; j < nP && ok; ++j) {
+  long long idx = static_cast<long long>(z0) * plane_elems + static_cast<long long>(gy) * p.pitch + gx;
+  float* const out_base = p.fields + p.prev * p.slot_elems;
+  int j = 0;
+
+  // One output plane z = z0 + j.
+  auto plane = [&]() -> bool {
     const int sn = j + 2 * RZ;  // sequence number of plane z+R
     const int sc = j + RZ;      // sequence number of the centre plane z
     const int un = sn % T::NSU;
     const int uc = sc % T::NSU;
-    ok = mbar_wait_bounded(&fullU[un], (sn / T::NSU) & 1, abort_flag, kWaitLimitNs);
-    ok = __all_sync(0xffffffffu, ok);
-    if (!ok) break;
-#pragma unroll
-    for (int i = 0; i < 2 * RZ; ++i) q[i] = q[i + 1];
+    bool good = mbar_wait_bounded(&fullU[un], (sn / T::NSU) & 1, abort_flag, kWaitLimitNs);
+    if (!__all_sync(0xffffffffu, good)) return false;
     q[2 * RZ] = lds4(Ubase + un * (T::U_STRIDE / 4) + lofs);
     const float4 c = q[RZ];
     const float* Uc = Ubase + uc * (T::U_STRIDE / 4) + lofs;
 
-    // Laplacian: centre, streamed axis from registers, axis 1 and x from smem
-    float4 lap = make_float4(p.c0 * c.x, p.c0 * c.y, p.c0 * c.z, p.c0 * c.w);
+    // Laplacian on two packed pairs (points 0,1 and 2,3 of the quad)
+    float2 la = __fmul2_rn(c0v, make_float2(c.x, c.y));
+    float2 lb = __fmul2_rn(c0v, make_float2(c.z, c.w));
 #pragma unroll
-    for (int k = 1; k <= RZ; ++k) fma4(lap, p.cz[k - 1], q[RZ - k], q[RZ + k]);
+    for (int k = 1; k <= RZ; ++k) {
+      const float4 a = q[RZ - k];
+      const float4 b = q[RZ + k];
+      la = __ffma2_rn(czv[k - 1], __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y)), la);
+      lb = __ffma2_rn(czv[k - 1], __fadd2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w)), lb);
+    }
 #pragma unroll
-    for (int k = 1; k <= R; ++k) fma4(lap, p.cy[k - 1], lds4(Uc - k * T::UW), lds4(Uc + k * T::UW));
+    for (int k = 1; k <= R; ++k) {
+      const float4 a = lds4(Uc - k * T::UW);
+      const float4 b = lds4(Uc + k * T::UW);
+      la = __ffma2_rn(cyv[k - 1], __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y)), la);
+      lb = __ffma2_rn(cyv[k - 1], __fadd2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w)), lb);
+    }
     {
-      constexpr int NQ = T::HX / 4;  // halo quads per side
+      constexpr int NH = T::HX / 4;  // halo quads per side
       float v[4 + 2 * T::HX];
 #pragma unroll
-      for (int k = 0; k < NQ; ++k) {
+      for (int k = 0; k < NH; ++k) {
         const float4 l = lds4(Uc - 4 * (k + 1));
         const float4 r = lds4(Uc + 4 * (k + 1));
         v[T::HX - 4 * (k + 1) + 0] = l.x;
@@ -265,39 +305,49 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS)
       v[T::HX + 3] = c.w;
 #pragma unroll
       for (int k = 1; k <= R; ++k) {
-        lap.x = fmaf(p.cx[k - 1], v[T::HX + 0 - k] + v[T::HX + 0 + k], lap.x);
-        lap.y = fmaf(p.cx[k - 1], v[T::HX + 1 - k] + v[T::HX + 1 + k], lap.y);
-        lap.z = fmaf(p.cx[k - 1], v[T::HX + 2 - k] + v[T::HX + 2 + k], lap.z);
-        lap.w = fmaf(p.cx[k - 1], v[T::HX + 3 - k] + v[T::HX + 3 + k], lap.w);
+        constexpr int H = T::HX;
+        if (k % 2 == 0) {
+          // even offsets keep the pairs register-aligned
+          la = __ffma2_rn(cxv[k - 1], __fadd2_rn(make_float2(v[H - k], v[H + 1 - k]), make_float2(v[H + k], v[H + 1 + k])), la);
+          lb = __ffma2_rn(cxv[k - 1], __fadd2_rn(make_float2(v[H + 2 - k], v[H + 3 - k]), make_float2(v[H + 2 + k], v[H + 3 + k])), lb);
+        } else {
+          la.x = fmaf(p.cx[k - 1], v[H + 0 - k] + v[H + 0 + k], la.x);
+          la.y = fmaf(p.cx[k - 1], v[H + 1 - k] + v[H + 1 + k], la.y);
+          lb.x = fmaf(p.cx[k - 1], v[H + 2 - k] + v[H + 2 + k], lb.x);
+          lb.y = fmaf(p.cx[k - 1], v[H + 3 - k] + v[H + 3 + k], lb.y);
+        }
       }
     }
+    const float4 lap = make_float4(la.x, la.y, lb.x, lb.y);
 
     const int ps = j % T::NSP;
-    ok = mbar_wait_bounded(&fullP[ps], (j / T::NSP) & 1, abort_flag, kWaitLimitNs);
-    ok = __all_sync(0xffffffffu, ok);
-    if (!ok) break;
+    good = mbar_wait_bounded(&fullP[ps], (j / T::NSP) & 1, abort_flag, kWaitLimitNs);
+    if (!__all_sync(0xffffffffu, good)) return false;
     const unsigned char* Pst = Pbase + ps * L::P_BYTES;
-    const int tofs = (ty * T::BX + 4 * tx) * 4;  // byte offset of this quad in a tile
     const float4 prev = *reinterpret_cast<const float4*>(Pst + L::PREV_OFF + tofs);
     const float4 cm = *reinterpret_cast<const float4*>(Pst + L::CM_OFF + tofs);
 
     const int gz = z0 + j;
-    const float eyz = ey + (NDIM == 3 ? sponge_term(gz, p.NZ, p.nblz, p.emz) : 0.f);
+    const float ez = NDIM == 3 ? sponge_term(gz, p.NZ, p.nblz, p.emz) : 0.f;
     float4 out;
-    {
+    if (exy_max + ez == 0.f) {
+      // undamped: new = 2 cur - prev + cm L (the damped formula at k = 0)
+      out.x = fmaf(cm.x, lap.x, fmaf(-1.f, prev.x, 2.f * c.x));
+      out.y = fmaf(cm.y, lap.y, fmaf(-1.f, prev.y, 2.f * c.y));
+      out.z = fmaf(cm.z, lap.z, fmaf(-1.f, prev.z, 2.f * c.z));
+      out.w = fmaf(cm.w, lap.w, fmaf(-1.f, prev.w, 2.f * c.w));
+    } else {
       float omk;
-      float inv = damp_inv(ex[0] + eyz, cm.x, p.half_inv_dt, omk);
-      out.x = (2.f * c.x - omk * prev.x + cm.x * lap.x) * inv;
-      inv = damp_inv(ex[1] + eyz, cm.y, p.half_inv_dt, omk);
-      out.y = (2.f * c.y - omk * prev.y + cm.y * lap.y) * inv;
-      inv = damp_inv(ex[2] + eyz, cm.z, p.half_inv_dt, omk);
-      out.z = (2.f * c.z - omk * prev.z + cm.z * lap.z) * inv;
-      inv = damp_inv(ex[3] + eyz, cm.w, p.half_inv_dt, omk);
-      out.w = (2.f * c.w - omk * prev.w + cm.w * lap.w) * inv;
+      float inv = damp_inv(exy[0] + ez, cm.x, p.half_inv_dt, omk);
+      out.x = fmaf(cm.x, lap.x, fmaf(-omk, prev.x, 2.f * c.x)) * inv;
+      inv = damp_inv(exy[1] + ez, cm.y, p.half_inv_dt, omk);
+      out.y = fmaf(cm.y, lap.y, fmaf(-omk, prev.y, 2.f * c.y)) * inv;
+      inv = damp_inv(exy[2] + ez, cm.z, p.half_inv_dt, omk);
+      out.z = fmaf(cm.z, lap.z, fmaf(-omk, prev.z, 2.f * c.z)) * inv;
+      inv = damp_inv(exy[3] + ez, cm.w, p.half_inv_dt, omk);
+      out.w = fmaf(cm.w, lap.w, fmaf(-omk, prev.w, 2.f * c.w)) * inv;
     }
-
-    const long long idx = gz * plane_elems + static_cast<long long>(gy) * p.pitch + gx;
-    if (store_ok) *reinterpret_cast<float4*>(p.fields + p.prev * p.slot_elems + idx) = out;
+    if (store_ok) *reinterpret_cast<float4*>(out_base + idx) = out;
 
     if constexpr (mode_is_snap(MODE)) {
       if constexpr (FMT == 0) {
@@ -331,6 +381,16 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS)
     if (lane == 0) {
       mbar_arrive(&emptyU[uc]);
       mbar_arrive(&emptyP[ps]);
+    }
+    return true;
+  };
+
+  if (ok) {
+    for (; j < nP; ++j, idx += plane_elems) {
+      ok = plane();
+      if (!ok) break;
+#pragma unroll
+      for (int i = 0; i < 2 * RZ; ++i) q[i] = q[i + 1];
     }
   }
   if (!ok && lane == 0) {
