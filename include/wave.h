@@ -215,6 +215,38 @@ WAVE_API double wave_dt_max(int ndim, const double* spacing, int space_order, do
  * t_n = n dt, n = 0..nt-1 (Sec. V-D source); q_out: nt float32 (host or device). */
 WAVE_API int wave_ricker(float* q_out, int nt, float dt, float f0, float t0);
 
+/* ---- allocation-free entry point ------------------------------------------ */
+
+/* The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory at the time they need the objective: code that
+ * runs while a stream is being captured into a CUDA graph, plug-ins whose host
+ * application owns every device allocation through its own pool, or services
+ * that must not touch the allocator once a run has started.
+ *
+ * wave_objective_noalloc computes the residual r = d - d_obs and the objective
+ * phi = 0.5 * sum r^2 (FP64 accumulation) of Eq. 2 for n receiver samples, the
+ * same values wave_gradient returns in resid_out / phi_out, without creating a
+ * context and without calling cudaMalloc, cudaFree or any allocating routine.
+ * Its scratch is a file-scope device array of WAVE_OBJECTIVE_NOALLOC_MAX_N /
+ * WAVE_OBJECTIVE_NOALLOC_CHUNK + 1 doubles (256 KiB plus 8 bytes) that every
+ * GPU which loads the library holds until the process exits.
+ *   d, d_obs: device arrays of n float32 on the current CUDA device;
+ *   r_out:    device array of n float32 receiving r, or NULL;
+ *   phi_out:  host double receiving phi;
+ *   stream:   CUDA stream (NULL = legacy default); the call returns after the
+ *             stream has completed its work.
+ * The first call on a device looks up the scratch array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call on a device shares the same scratch and overwrites it; calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Nothing in the scratch needs to start at zero.
+ * Errors: INVALID_ARG (NULL pointer, n < 0, n > WAVE_OBJECTIVE_NOALLOC_MAX_N,
+ * or an array that is not device memory of the current device); CUDA. */
+#define WAVE_OBJECTIVE_NOALLOC_CHUNK 8192LL
+#define WAVE_OBJECTIVE_NOALLOC_MAX_N 268435456LL /* 2^28 samples */
+WAVE_API int wave_objective_noalloc(const float* d, const float* d_obs, float* r_out, int64_t n,
+                                    double* phi_out, void* stream);
+
 /* ---- instrumentation --------------------------------------------------- */
 
 /* Kernel kinds for wave_context_kernel_stats. */

@@ -83,6 +83,7 @@ _SIGS = {
     "wave_context_kernel_stats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                                  ctypes.POINTER(ctypes.c_double)]),
     "wave_context_reset_stats": (ctypes.c_int, [_P]),
+    "wave_objective_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), _P]),
 }
 
 _lib = None
@@ -381,6 +382,20 @@ def wave_ricker(nt, dt, f0, t0=None, out=None):
     if rc != WAVE_OK:
         raise WaveError(rc, "bad arguments to wave_ricker")
     return out
+
+
+def wave_objective_noalloc(d, d_obs, r_out=None, stream=None):
+    """(phi, r) of Eq. 2 for device tensors d, d_obs without any allocation in
+    the library (r is written into ``r_out`` when given)."""
+    d = _f32(d)
+    d_obs = _f32(d_obs)
+    n = int(d.numel()) if _is_torch(d) else int(d.size)
+    phi = ctypes.c_double()
+    st = stream if stream is not None else _stream_for(d, d_obs)
+    rc = lib().wave_objective_noalloc(_ptr(d), _ptr(d_obs), _ptr(r_out), n, ctypes.byref(phi), st)
+    if rc != WAVE_OK:
+        raise WaveError(rc, "wave_objective_noalloc failed")
+    return phi.value, r_out
 
 
 def wave_error_string(code):
