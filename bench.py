@@ -51,8 +51,12 @@ def parse_args():
     ap.add_argument("--so", type=int, default=8)
     ap.add_argument("--nbl", type=int, default=40)
     ap.add_argument("--snap", default="checkpoint_fp32")
-    ap.add_argument("--mode", default="gradient", choices=["gradient", "forward"],
-                    help="gradient: one FWI gradient per step (default); forward: one forward modelling per step")
+    ap.add_argument("--mode", default="gradient", choices=["gradient", "forward", "serve"],
+                    help="gradient: one FWI gradient per step (default); forward: one forward modelling per step; "
+                         "serve: a Poisson stream of shot-modelling requests through the continuous-batching server")
+    ap.add_argument("--requests", type=int, default=400, help="serve mode: number of requests")
+    ap.add_argument("--budget-gb", type=float, default=64.0, help="serve mode: HBM budget for resident requests")
+    ap.add_argument("--max-resident", type=int, default=32, help="serve mode: stream slots")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-nz", type=int, default=8, help="physical depth points of the CPU sample")
@@ -385,6 +389,75 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+def run_serve(args, rank, world, local_rank):
+    """Served shot modelling: seeded request stream (half 2D N^2, N in [201, 1001];
+    half 3D N^3, N in [128, 320]; orders 4/8/16; nt in [500, 2000]; layered
+    1.5-4.5 km/s), Poisson arrivals at 80 % of the capacity measured on a burst
+    of the first requests; each rank serves its own stream."""
+    import torch
+    from paper_1608_08658_gb300 import inputs, serve, wave
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    reqs = inputs.serving_requests(args.requests, seed=99 + rank)
+    budget = int(args.budget_gb * (1 << 30))
+    server = serve.ShotServer(device=local_rank, hbm_budget_bytes=budget, max_resident=args.max_resident)
+    # capacity from a burst (all arriving at once) of the first requests
+    nb = min(len(reqs), max(8, args.requests // 10))
+    burst = server.run(reqs[:nb], np.zeros(nb))
+    capacity = nb / burst.wall
+    rate = 0.8 * capacity
+    arrivals = serve.poisson_arrivals(len(reqs), rate, seed=99 + rank)
+    server.ctx.reset_stats()
+    clocks = ClockSampler(local_rank if world > 1 else None) if rank == 0 else None
+    torch.cuda.synchronize()
+    stats = server.run(reqs, arrivals)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    launches = server.ctx.kernel_stats(-1)[0]
+    summ = stats.summary()
+    wall = stats.wall
+    if dist:
+        t = torch.tensor([wall], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        wall = float(t.item())
+    shots = world * len(stats.results) / wall
+    pts = 0.0
+    h2d = d2h = 0
+    for r in reqs:
+        ncomp = (r["N"] + 2 * r["nbl"]) ** r["ndim"]
+        pts += ncomp * (r["nt"] - 1)
+        src, rec = inputs.request_points(r)
+        h2d += 4 * (r["N"] + r["nt"] + src.size + rec.size)
+        d2h += 4 * r["nt"] * len(rec)
+    server.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": shots, "unit": "shots/s", "n_gpus": world, "steps": len(reqs),
+                "warmup": nb, "ms_per_step": 1e3 * wall / max(1, len(stats.results)), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "served shot modelling: Poisson stream of %d requests (2D 201^2..1001^2 / "
+                                       "3D 128^3..320^3, orders 4/8/16, nt 500-2000, layered 1.5-4.5 km/s, "
+                                       "1 Ricker 10 Hz, 100-1000 receivers)" % len(reqs),
+                           "arrival_rate_per_s": rate, "burst_capacity_shots_per_s": capacity,
+                           "hbm_budget_gb": args.budget_gb, "max_resident": args.max_resident,
+                           "graph_chunk_steps": 32, "l2": "fields of the 3D requests exceed L2"},
+                "p50_latency_s": summ["p50_latency_s"], "p99_latency_s": summ["p99_latency_s"],
+                "mean_latency_s": summ["mean_latency_s"], "max_resident": summ["max_resident"],
+                "peak_workspace_gb": summ["peak_workspace_bytes"] / 2 ** 30,
+                "point_updates_gpts_per_s": world * pts / wall / 1e9,
+                "roofline": None, "cpu_baseline": None,
+                "e2e": {"value": shots, "unit": "shots/s", "h2d_bytes_per_step": int(h2d / len(reqs)),
+                        "d2h_bytes_per_step": int(d2h / len(reqs))},
+                "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def ctypes_stream(stream):
     import ctypes
     return ctypes.c_void_p(stream.cuda_stream)
@@ -399,6 +472,8 @@ def main():
         print("warning: --gpus %d but WORLD_SIZE %d" % (args.gpus, world), file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.mode == "serve":
+        return run_serve(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 

@@ -200,6 +200,52 @@ WAVE_API int wave_jacobian_adjoint(wave_context* ctx, const wave_geometry* geom,
                           const float* y, float* grad_out, float* d_out,
                           int snap_mode, float dt, int nt, int space_order, void* stream);
 
+/* ---- resident requests (serving) ------------------------------------------ */
+
+/* A session is one forward-modelling request (Listing 1) kept resident on the
+ * device so that many requests of different grids and space orders can be in
+ * flight at once, each on its own CUDA stream, and advanced a few steps at a
+ * time by a host scheduler (continuous batching).  Its device memory (two
+ * wavefield slots, coefficients, staged model and source traces, receiver
+ * data, point structures) is allocated at creation, counted against the
+ * context's budget and released by wave_session_destroy.  Steps are issued as
+ * replays of a CUDA graph of `graph_chunk` steps captured at creation (the
+ * sparse kernels read the time row from a device counter), plus ordinary
+ * launches for the steps that do not fill a whole chunk.  Results are the same
+ * as wave_forward's for the same inputs. */
+typedef struct wave_session wave_session;
+
+/* Device bytes a session for these arguments would hold (admission by HBM
+ * footprint).  Validates the geometry and points like wave_forward. */
+WAVE_API int wave_session_footprint(wave_context* ctx, const wave_geometry* geom, const wave_points* src,
+                                    const wave_points* rec, int nt, int space_order, size_t* bytes_out);
+
+/* Create a session: copies m [N_z][N_y][N_x] and q [nt][n_s] (host or device)
+ * into its own memory, checks dt, builds the point structures, captures the
+ * step graph (graph_chunk even, 0 = no graph) on `stream`; returns after the
+ * stream has completed the set-up.  Errors: as wave_forward. */
+WAVE_API int wave_session_create(wave_context* ctx, wave_session** session, const wave_geometry* geom,
+                                 const float* m, const wave_points* src, const float* q, const wave_points* rec,
+                                 float dt, int nt, int space_order, int graph_chunk, void* stream);
+
+/* Enqueue about `steps` more time steps (whole graph chunks when possible) on
+ * the session's stream without waiting; *steps_left receives the number of
+ * steps not yet enqueued. */
+WAVE_API int wave_session_advance(wave_session* session, int steps, int* steps_left);
+
+/* *done = 1 when every step has been enqueued and has completed. */
+WAVE_API int wave_session_query(wave_session* session, int* done);
+
+/* Copy the receiver data [nt][n_r] to d_out (host or device) once all steps
+ * are enqueued; waits for the session's stream. */
+WAVE_API int wave_session_read(wave_session* session, float* d_out);
+
+/* Release the session's device memory (waits for its stream). NULL accepted. */
+WAVE_API int wave_session_destroy(wave_session* session);
+
+/* Budget left for new sessions and workspace (0 when the context has no cap). */
+WAVE_API size_t wave_context_budget_free(const wave_context* ctx);
+
 /* ---- helpers (host-side, no device work) ---------------------------------- */
 
 /* Centred second-derivative weights [w_0, w_1, .., w_R], R = space_order/2

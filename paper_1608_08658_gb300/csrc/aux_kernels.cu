@@ -273,6 +273,42 @@ __global__ void unpack_kernel(GridDims g, const float* __restrict__ dense, float
   }
 }
 
+// Variants used inside captured CUDA graphs: the time row is read from a
+// device counter (the number of steps completed before the replay) plus the
+// position of the step within the captured chunk.
+__global__ void inject_counter_kernel(InjectSet is, const float* __restrict__ q, long long ns,
+                                      const int* __restrict__ counter, int offset, float* __restrict__ field) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= is.n) return;
+  const float* vals = q + static_cast<long long>(*counter + offset) * ns;
+  float s = 0.f;
+  for (int e = is.rowptr[k]; e < is.rowptr[k + 1]; ++e) s = fmaf(is.w[e], vals[is.pidx[e]], s);
+  field[is.cell[k]] += is.coef[k] * s;
+}
+
+__global__ void gather_counter_kernel(GatherSet gs, const float* __restrict__ field, float* __restrict__ d,
+                                      const int* __restrict__ counter, int offset) {
+  const int C = gs.ndim == 3 ? 8 : 4;
+  const long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  const long long pt = t / C;
+  const int c = static_cast<int>(t % C);
+  const bool valid = pt < gs.n;
+  float v = 0.f;
+  if (valid) {
+    const float fx = gs.frac[3 * pt], fy = gs.frac[3 * pt + 1], fz = gs.frac[3 * pt + 2];
+    const int bx = c & 1, by = (c >> 1) & 1, bz = (c >> 2) & 1;
+    float w = (bx ? fx : 1.f - fx) * (by ? fy : 1.f - fy);
+    if (gs.ndim == 3) w *= (bz ? fz : 1.f - fz);
+    v = w * field[gs.base[pt] + bx + by * gs.sy + bz * gs.sz];
+  }
+  for (int off = C / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if (valid && c == 0) d[static_cast<long long>(*counter + offset) * gs.n + pt] = v;
+}
+
+__global__ void counter_add_kernel(int* counter, int delta) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *counter += delta;
+}
+
 __global__ void fill_zero_kernel(float* p, long long n) {
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
        i += static_cast<long long>(gridDim.x) * blockDim.x)
@@ -360,6 +396,27 @@ cudaError_t launch_pack_state(const GridDims& g, const float* field, float* dens
 cudaError_t launch_unpack_state(const GridDims& g, const float* dense, float* field, cudaStream_t s) {
   const long long n = static_cast<long long>(g.NZ) * g.NY * g.NX;
   unpack_kernel<<<blocks_for(n), kThreads, 0, s>>>(g, dense, field);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inject_counter(const InjectSet& is, const float* q, long long ns, const int* counter, int offset,
+                                  float* field, cudaStream_t s) {
+  if (is.n == 0) return cudaSuccess;
+  inject_counter_kernel<<<(is.n + kThreads - 1) / kThreads, kThreads, 0, s>>>(is, q, ns, counter, offset, field);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_counter(const GatherSet& gs, const float* field, float* d, const int* counter, int offset,
+                                  cudaStream_t s) {
+  if (gs.n == 0) return cudaSuccess;
+  const long long lanes = gs.n * (gs.ndim == 3 ? 8 : 4);
+  const long long blocks = (lanes + kThreads - 1) / kThreads;
+  gather_counter_kernel<<<static_cast<unsigned>(blocks), kThreads, 0, s>>>(gs, field, d, counter, offset);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_counter_add(int* counter, int delta, cudaStream_t s) {
+  counter_add_kernel<<<1, 32, 0, s>>>(counter, delta);
   return cudaGetLastError();
 }
 

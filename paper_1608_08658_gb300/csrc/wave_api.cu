@@ -433,19 +433,9 @@ struct Work {
   StepMaps maps;
 };
 
-// Field buffer, coefficient field and their tensor maps.
-int prepare_fields(wave_context* ctx, Prob& P, const float* m_dev, cudaStream_t s, bool need_grad, Work* W) {
-  const GridDims& g = P.g;
-  void* p = nullptr;
-  TRY(ws_get(ctx, "fields", 4 * P.slot_elems * sizeof(float), &p));
-  W->fields = static_cast<float*>(p);
-  TRY(ws_get(ctx, "cm", P.slot_elems * sizeof(float), &p));
-  W->cm = static_cast<float*>(p);
-  if (need_grad) {
-    TRY(ws_get(ctx, "grad", P.slot_elems * sizeof(float), &p));
-    W->grad = static_cast<float*>(p);
-  }
-  // model checks: positive, finite, and dt within the stability limit
+// Model checks (positive, finite, dt within the stability limit) and the
+// coefficient field cm = dt^2/m on the computational grid.
+int setup_model(wave_context* ctx, Prob& P, const float* m_dev, float* cm, cudaStream_t s) {
   CK(cudaMemsetAsync(ctx->d_minmax, 0, 2 * sizeof(unsigned int), s));
   CK(cudaMemsetAsync(ctx->d_minmax, 0xff, sizeof(unsigned int), s));
   TRY(launch(ctx, WAVE_KERNEL_OTHER, s, [&] { return launch_minmax(m_dev, P.phys_elems, ctx->d_minmax, s); }));
@@ -461,33 +451,58 @@ int prepare_fields(wave_context* ctx, Prob& P, const float* m_dev, cudaStream_t 
   if (double(P.dt) > dtm)
     return fail(ctx, WAVE_ERR_UNSTABLE_DT, "dt = %g ms exceeds the stability limit %g ms (v_max = %g km/s)",
                 double(P.dt), dtm, vmax);
-  TRY(launch(ctx, WAVE_KERNEL_OTHER, s, [&] {
-    return launch_setup_cm(g, m_dev, W->cm, static_cast<float>(double(P.dt) * P.dt), s);
-  }));
-  // tensor maps
+  return launch(ctx, WAVE_KERNEL_OTHER, s, [&] {
+    return launch_setup_cm(P.g, m_dev, cm, static_cast<float>(double(P.dt) * P.dt), s);
+  });
+}
+
+// Tensor maps over a field buffer of `nslots` slots, the coefficient field and
+// (optionally) the gradient.
+int make_field_maps(wave_context* ctx, Prob& P, float* fields, int nslots, float* cm, float* grad, Work* W) {
+  const GridDims& g = P.g;
   const int hx = step_hx(P.R);
   const int by = step_by(P.R, P.ndim);
   const int bx = step_bx();
   {
-    cuuint64_t dims[4] = {(cuuint64_t)g.NX, (cuuint64_t)g.NY, (cuuint64_t)g.NZ, 4};
+    cuuint64_t dims[4] = {(cuuint64_t)g.NX, (cuuint64_t)g.NY, (cuuint64_t)g.NZ, (cuuint64_t)nslots};
     cuuint64_t str[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.pitch * g.NY * 4, (cuuint64_t)P.slot_elems * 4};
     cuuint32_t boxu[4] = {(cuuint32_t)(bx + 2 * hx), (cuuint32_t)(by + 2 * P.R), 1, 1};
     cuuint32_t boxp[4] = {(cuuint32_t)bx, (cuuint32_t)by, 1, 1};
-    TRY(make_map(ctx, &W->maps.u, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, W->fields, dims, str, boxu));
-    TRY(make_map(ctx, &W->maps.p, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, W->fields, dims, str, boxp));
+    TRY(make_map(ctx, &W->maps.u, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, fields, dims, str, boxu));
+    TRY(make_map(ctx, &W->maps.p, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, fields, dims, str, boxp));
   }
   {
     cuuint64_t dims[3] = {(cuuint64_t)g.NX, (cuuint64_t)g.NY, (cuuint64_t)g.NZ};
     cuuint64_t str[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.pitch * g.NY * 4};
     cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
-    TRY(make_map(ctx, &W->maps.cm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, W->cm, dims, str, box));
-    if (need_grad) TRY(make_map(ctx, &W->maps.g, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, W->grad, dims, str, box));
+    TRY(make_map(ctx, &W->maps.cm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, cm, dims, str, box));
+    if (grad) TRY(make_map(ctx, &W->maps.g, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, grad, dims, str, box));
     else W->maps.g = W->maps.cm;
   }
   W->maps.s = W->maps.p;
-  P.sp.fields = W->fields;
+  W->fields = fields;
+  W->cm = cm;
+  W->grad = grad;
+  P.sp.fields = fields;
   P.sp.status = ctx->d_status;
   return WAVE_OK;
+}
+
+// Field buffer (4 slots), coefficient field, optional gradient from the
+// context workspace, with the model set-up and the tensor maps.
+int prepare_fields(wave_context* ctx, Prob& P, const float* m_dev, cudaStream_t s, bool need_grad, Work* W) {
+  void* p = nullptr;
+  TRY(ws_get(ctx, "fields", 4 * P.slot_elems * sizeof(float), &p));
+  float* fields = static_cast<float*>(p);
+  TRY(ws_get(ctx, "cm", P.slot_elems * sizeof(float), &p));
+  float* cm = static_cast<float*>(p);
+  float* grad = nullptr;
+  if (need_grad) {
+    TRY(ws_get(ctx, "grad", P.slot_elems * sizeof(float), &p));
+    grad = static_cast<float*>(p);
+  }
+  TRY(setup_model(ctx, P, m_dev, cm, s));
+  return make_field_maps(ctx, P, fields, 4, cm, grad, W);
 }
 
 int snapshot_map(wave_context* ctx, Prob& P, int fmt, void* store, int levels, CUtensorMap* map) {
@@ -511,7 +526,19 @@ uint64_t fnv(uint64_t h, const void* p, size_t n) {
   return h;
 }
 
-int prepare_points(wave_context* ctx, Prob& P, const wave_points* pts, cudaStream_t s, PointSetDev** out) {
+// Host-side interpolation structures of one point set: per point the base
+// cell and fractions (gather), and a CSR over unique cells (injection).
+struct PointsHost {
+  long long n = 0;
+  uint64_t key = 0;
+  std::vector<long long> base;
+  std::vector<float> frac;
+  std::vector<long long> cells;
+  std::vector<int> rowptr, pidx;
+  std::vector<float> wts;
+};
+
+int build_points_host(wave_context* ctx, Prob& P, const wave_points* pts, PointsHost* H) {
   if (!pts) return fail(ctx, WAVE_ERR_INVALID_ARG, "point set is NULL");
   const long long n = pts->n;
   if (n < 0 || n > (1LL << 28)) return fail(ctx, WAVE_ERR_INVALID_ARG, "point count %lld out of range", n);
@@ -532,16 +559,12 @@ int prepare_points(wave_context* ctx, Prob& P, const wave_points* pts, cudaStrea
   key = fnv(key, P.o, sizeof(P.o));
   key = fnv(key, P.lo, sizeof(P.lo));
   key = fnv(key, P.hi, sizeof(P.hi));
-  for (auto& e : ctx->pts) {
-    if (e.valid && e.key == key && e.n == n) {
-      *out = &e;
-      return WAVE_OK;
-    }
-  }
+  H->n = n;
+  H->key = key;
   const GridDims& g = P.g;
   const long long sy = g.pitch, sz = static_cast<long long>(g.pitch) * g.NY;
-  std::vector<long long> base(static_cast<size_t>(n));
-  std::vector<float> frac(static_cast<size_t>(n) * 3, 0.f);
+  H->base.assign(static_cast<size_t>(n), 0);
+  H->frac.assign(static_cast<size_t>(n) * 3, 0.f);
   struct Trip {
     long long cell;
     int p;
@@ -567,8 +590,8 @@ int prepare_points(wave_context* ctx, Prob& P, const wave_points* pts, cudaStrea
       f[a] = fr;
       b += k * (a == 0 ? 1 : (a == 1 ? sy : sz));
     }
-    base[i] = b;
-    for (int a = 0; a < 3; ++a) frac[i * 3 + a] = static_cast<float>(f[a]);
+    H->base[i] = b;
+    for (int a = 0; a < 3; ++a) H->frac[i * 3 + a] = static_cast<float>(f[a]);
     for (int cc = 0; cc < C; ++cc) {
       double w = 1.0;
       long long idx = b;
@@ -583,53 +606,83 @@ int prepare_points(wave_context* ctx, Prob& P, const wave_points* pts, cudaStrea
   std::sort(trips.begin(), trips.end(), [](const Trip& x, const Trip& y) {
     return x.cell < y.cell || (x.cell == y.cell && x.p < y.p);
   });
-  std::vector<long long> cells;
-  std::vector<int> rowptr(1, 0), pidx;
-  std::vector<float> wts;
+  H->cells.clear();
+  H->rowptr.assign(1, 0);
+  H->pidx.clear();
+  H->wts.clear();
   for (size_t k = 0; k < trips.size(); ++k) {
     if (k == 0 || trips[k].cell != trips[k - 1].cell) {
-      if (k > 0) rowptr.push_back(static_cast<int>(k));
-      cells.push_back(trips[k].cell);
+      if (k > 0) H->rowptr.push_back(static_cast<int>(k));
+      H->cells.push_back(trips[k].cell);
     }
-    pidx.push_back(trips[k].p);
-    wts.push_back(trips[k].w);
+    H->pidx.push_back(trips[k].p);
+    H->wts.push_back(trips[k].w);
   }
-  rowptr.push_back(static_cast<int>(trips.size()));
-  if (cells.empty()) rowptr.assign(1, 0);
-  // store in a cache slot
+  H->rowptr.push_back(static_cast<int>(trips.size()));
+  if (H->cells.empty()) H->rowptr.assign(1, 0);
+  return WAVE_OK;
+}
+
+// Device bytes of the uploaded structures of a point set (each array rounded
+// like a workspace allocation).
+size_t points_device_bytes(const PointsHost& H) {
+  auto r = [](size_t b) { return round_up(std::max<size_t>(b, 256), 256); };
+  return r(std::max<size_t>(1, H.base.size()) * 8) + r(std::max<size_t>(1, H.frac.size()) * 4) +
+         r(std::max<size_t>(1, H.cells.size()) * 8) + r(H.rowptr.size() * 4) +
+         r(std::max<size_t>(1, H.pidx.size()) * 4) + r(std::max<size_t>(1, H.wts.size()) * 4) +
+         r(std::max<size_t>(1, H.cells.size()) * 4);
+}
+
+// Copy host structures into device arrays already placed in `e`.
+int upload_points(wave_context* ctx, const PointsHost& H, PointSetDev& e, cudaStream_t s) {
+  if (H.n > 0) {
+    CK(cudaMemcpyAsync(e.base, H.base.data(), H.base.size() * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(e.frac, H.frac.data(), H.frac.size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(e.cell, H.cells.data(), H.cells.size() * 8, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(e.pidx, H.pidx.data(), H.pidx.size() * 4, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(e.w, H.wts.data(), H.wts.size() * 4, cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemcpyAsync(e.rowptr, H.rowptr.data(), H.rowptr.size() * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // the host vectors may go out of scope after this
+  e.n = H.n;
+  e.ncell = static_cast<int>(H.cells.size());
+  e.key = H.key;
+  e.valid = true;
+  return WAVE_OK;
+}
+
+// Point structures for one call, cached in the context (keyed by coordinates
+// and geometry) so repeated calls with the same points skip the build.
+int prepare_points(wave_context* ctx, Prob& P, const wave_points* pts, cudaStream_t s, PointSetDev** out) {
+  PointsHost H;
+  TRY(build_points_host(ctx, P, pts, &H));
+  for (auto& e : ctx->pts) {
+    if (e.valid && e.key == H.key && e.n == H.n) {
+      *out = &e;
+      return WAVE_OK;
+    }
+  }
   PointSetDev& e = ctx->pts[ctx->pts_next];
   ctx->pts_next = (ctx->pts_next + 1) % 4;
   e.valid = false;
   const int slot = static_cast<int>(&e - ctx->pts);
   e.tag = "pts" + std::to_string(slot) + "_";
   void* p = nullptr;
-  TRY(ws_get(ctx, e.tag + "base", std::max<size_t>(1, base.size()) * 8, &p));
+  TRY(ws_get(ctx, e.tag + "base", std::max<size_t>(1, H.base.size()) * 8, &p));
   e.base = static_cast<long long*>(p);
-  TRY(ws_get(ctx, e.tag + "frac", std::max<size_t>(1, frac.size()) * 4, &p));
+  TRY(ws_get(ctx, e.tag + "frac", std::max<size_t>(1, H.frac.size()) * 4, &p));
   e.frac = static_cast<float*>(p);
-  TRY(ws_get(ctx, e.tag + "cell", std::max<size_t>(1, cells.size()) * 8, &p));
+  TRY(ws_get(ctx, e.tag + "cell", std::max<size_t>(1, H.cells.size()) * 8, &p));
   e.cell = static_cast<long long*>(p);
-  TRY(ws_get(ctx, e.tag + "rowptr", rowptr.size() * 4, &p));
+  TRY(ws_get(ctx, e.tag + "rowptr", H.rowptr.size() * 4, &p));
   e.rowptr = static_cast<int*>(p);
-  TRY(ws_get(ctx, e.tag + "pidx", std::max<size_t>(1, pidx.size()) * 4, &p));
+  TRY(ws_get(ctx, e.tag + "pidx", std::max<size_t>(1, H.pidx.size()) * 4, &p));
   e.pidx = static_cast<int*>(p);
-  TRY(ws_get(ctx, e.tag + "w", std::max<size_t>(1, wts.size()) * 4, &p));
+  TRY(ws_get(ctx, e.tag + "w", std::max<size_t>(1, H.wts.size()) * 4, &p));
   e.w = static_cast<float*>(p);
-  TRY(ws_get(ctx, e.tag + "coef", std::max<size_t>(1, cells.size()) * 4, &p));
+  TRY(ws_get(ctx, e.tag + "coef", std::max<size_t>(1, H.cells.size()) * 4, &p));
   e.coef = static_cast<float*>(p);
-  if (n > 0) {
-    CK(cudaMemcpyAsync(e.base, base.data(), base.size() * 8, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(e.frac, frac.data(), frac.size() * 4, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(e.cell, cells.data(), cells.size() * 8, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(e.pidx, pidx.data(), pidx.size() * 4, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(e.w, wts.data(), wts.size() * 4, cudaMemcpyHostToDevice, s));
-  }
-  CK(cudaMemcpyAsync(e.rowptr, rowptr.data(), rowptr.size() * 4, cudaMemcpyHostToDevice, s));
-  CK(cudaStreamSynchronize(s));  // host vectors go out of scope
-  e.n = n;
-  e.ncell = static_cast<int>(cells.size());
-  e.key = key;
-  e.valid = true;
+  TRY(upload_points(ctx, H, e, s));
   *out = &e;
   return WAVE_OK;
 }
@@ -1069,6 +1122,182 @@ int gradient_impl(wave_context* ctx, const wave_geometry* geom, const float* m, 
   return WAVE_OK;
 }
 
+// ---------------------------------------------------------------- sessions
+// Device bytes a resident forward-modelling request holds: two wavefield
+// slots, the coefficient field, staged model and source traces, receiver
+// data, point structures, the step counter.
+size_t session_bytes(const Prob& P, const PointsHost& hs, const PointsHost& hr, long long ns, long long nr) {
+  auto r = [](size_t b) { return round_up(std::max<size_t>(b, 256), 256); };
+  return r(2 * P.slot_elems * 4) + r(P.slot_elems * 4) + r(P.phys_elems * 4) + r(static_cast<size_t>(P.nt) * ns * 4) +
+         r(static_cast<size_t>(P.nt) * nr * 4) + points_device_bytes(hs) + points_device_bytes(hr) + r(4);
+}
+
+}  // namespace
+
+struct wave_session {
+  wave_context* ctx = nullptr;
+  cudaStream_t stream = nullptr;
+  Prob P;
+  Work W;
+  PointSetDev src, rec;
+  std::vector<std::pair<void*, size_t>> allocs;
+  float* q = nullptr;
+  float* d = nullptr;
+  int* counter = nullptr;
+  long long ns = 0, nr = 0;
+  int next = 0;      // next time step to enqueue (steps are n = 0 .. nt-2)
+  int chunk = 0;     // steps per captured graph (even)
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;
+};
+
+namespace {
+
+int sess_alloc(wave_session* S, size_t bytes, void** out) {
+  wave_context* ctx = S->ctx;
+  bytes = round_up(std::max<size_t>(bytes, 256), 256);
+  if (ctx->budget && ctx->held + bytes > ctx->budget)
+    return fail(ctx, WAVE_ERR_OUT_OF_MEMORY, "request needs %zu more bytes than the budget allows", bytes);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, WAVE_ERR_OUT_OF_MEMORY, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  S->allocs.push_back({p, bytes});
+  ctx->held += bytes;
+  *out = p;
+  return WAVE_OK;
+}
+
+void sess_free(wave_session* S) {
+  for (auto& a : S->allocs) {
+    cudaFree(a.first);
+    S->ctx->held -= a.second;
+  }
+  S->allocs.clear();
+}
+
+int sess_points(wave_session* S, const PointsHost& H, PointSetDev* e) {
+  void* p = nullptr;
+  TRY(sess_alloc(S, std::max<size_t>(1, H.base.size()) * 8, &p));
+  e->base = static_cast<long long*>(p);
+  TRY(sess_alloc(S, std::max<size_t>(1, H.frac.size()) * 4, &p));
+  e->frac = static_cast<float*>(p);
+  TRY(sess_alloc(S, std::max<size_t>(1, H.cells.size()) * 8, &p));
+  e->cell = static_cast<long long*>(p);
+  TRY(sess_alloc(S, H.rowptr.size() * 4, &p));
+  e->rowptr = static_cast<int*>(p);
+  TRY(sess_alloc(S, std::max<size_t>(1, H.pidx.size()) * 4, &p));
+  e->pidx = static_cast<int*>(p);
+  TRY(sess_alloc(S, std::max<size_t>(1, H.wts.size()) * 4, &p));
+  e->w = static_cast<float*>(p);
+  TRY(sess_alloc(S, std::max<size_t>(1, H.cells.size()) * 4, &p));
+  e->coef = static_cast<float*>(p);
+  return upload_points(S->ctx, H, *e, S->stream);
+}
+
+// Kernels of `count` steps starting at an even step; the time rows of the
+// sparse kernels come from the device counter so the same launches serve any
+// even start (used while capturing the session's graph).
+int enqueue_chunk_body(wave_session* S, int count, cudaStream_t s) {
+  wave_context* ctx = S->ctx;
+  Prob& P = S->P;
+  InjectSet isrc = inject_set(&S->src);
+  GatherSet grec = gather_set(P, &S->rec);
+  for (int i = 0; i < count; ++i) {
+    P.sp.cur = fslot(i);
+    P.sp.prev = fslot(i - 1);
+    cudaError_t e = launch_step(P.R, P.ndim, MODE_PLAIN, S->W.maps, P.sp, P.grid, s);
+    if (e == cudaSuccess && isrc.n > 0)
+      e = launch_inject_counter(isrc, S->q, S->ns, S->counter, i, slot_ptr(S->W, P, fslot(i + 1)), s);
+    if (e == cudaSuccess && S->nr > 0)
+      e = launch_gather_counter(grec, slot_ptr(S->W, P, fslot(i + 1)), S->d, S->counter, i + 1, s);
+    if (e != cudaSuccess) return fail(ctx, WAVE_ERR_CUDA, "launch during capture failed: %s", cudaGetErrorString(e));
+  }
+  cudaError_t e = launch_counter_add(S->counter, count, s);
+  if (e != cudaSuccess) return fail(ctx, WAVE_ERR_CUDA, "launch during capture failed: %s", cudaGetErrorString(e));
+  return WAVE_OK;
+}
+
+// Capture one chunk on a private stream (the caller's stream may be the legacy
+// default stream, which cannot be captured); the instantiated graph is then
+// launched into the session's stream.
+int session_capture(wave_session* S) {
+  wave_context* ctx = S->ctx;
+  cudaStream_t cs = nullptr;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  int rc = WAVE_OK;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    rc = fail(ctx, WAVE_ERR_CUDA, "stream capture failed to start: %s", cudaGetErrorString(e));
+  } else {
+    rc = enqueue_chunk_body(S, S->chunk, cs);
+    e = cudaStreamEndCapture(cs, &graph);
+    if (rc == WAVE_OK && e != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(ctx, WAVE_ERR_CUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    }
+  }
+  if (rc == WAVE_OK) {
+    e = cudaGraphInstantiate(&S->exec, graph, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(ctx, WAVE_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  return rc;
+}
+
+int session_create_impl(wave_context* ctx, wave_session* S, const wave_geometry* geom, const float* m,
+                        const wave_points* src, const float* q, const wave_points* rec, float dt, int nt, int so) {
+  TRY(check_common(ctx, geom, m));
+  Prob& P = S->P;
+  TRY(prepare(ctx, geom, dt, nt, so, &P));
+  wave_points empty{0, nullptr};
+  PointsHost hs, hr;
+  TRY(build_points_host(ctx, P, src ? src : &empty, &hs));
+  TRY(build_points_host(ctx, P, rec ? rec : &empty, &hr));
+  S->ns = hs.n;
+  S->nr = hr.n;
+  if (S->ns > 0 && !q) return fail(ctx, WAVE_ERR_INVALID_ARG, "source traces are NULL");
+  cudaStream_t s = S->stream;
+  void* p = nullptr;
+  TRY(sess_alloc(S, 2 * P.slot_elems * 4, &p));
+  float* fields = static_cast<float*>(p);
+  TRY(sess_alloc(S, P.slot_elems * 4, &p));
+  float* cm = static_cast<float*>(p);
+  TRY(sess_alloc(S, P.phys_elems * 4, &p));
+  float* md = static_cast<float*>(p);
+  TRY(sess_alloc(S, static_cast<size_t>(nt) * std::max<long long>(S->ns, 1) * 4, &p));
+  S->q = static_cast<float*>(p);
+  TRY(sess_alloc(S, static_cast<size_t>(nt) * std::max<long long>(S->nr, 1) * 4, &p));
+  S->d = static_cast<float*>(p);
+  TRY(sess_alloc(S, 4, &p));
+  S->counter = static_cast<int*>(p);
+  CK(cudaMemcpyAsync(md, m, P.phys_elems * 4, cudaMemcpyDefault, s));
+  if (S->ns > 0) CK(cudaMemcpyAsync(S->q, q, static_cast<size_t>(nt) * S->ns * 4, cudaMemcpyDefault, s));
+  TRY(sess_points(S, hs, &S->src));
+  TRY(sess_points(S, hr, &S->rec));
+  TRY(setup_model(ctx, P, md, cm, s));
+  TRY(make_field_maps(ctx, P, fields, 2, cm, nullptr, &S->W));
+  TRY(inject_coefficients(ctx, P, S->W, &S->src, s));
+  CK(cudaMemsetAsync(fields, 0, 2 * P.slot_elems * 4, s));
+  CK(cudaMemsetAsync(S->counter, 0, 4, s));
+  if (S->nr > 0) {
+    GatherSet grec = gather_set(P, &S->rec);
+    TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_gather(grec, slot_ptr(S->W, P, fslot(0)), S->d, s); }));
+  }
+  CK(cudaEventCreateWithFlags(&S->done, cudaEventDisableTiming));
+  S->next = 0;
+  if (S->chunk > 0 && nt - 1 >= S->chunk) TRY(session_capture(S));
+  return WAVE_OK;
+}
+
 }  // namespace
 
 // ============================================================================
@@ -1281,6 +1510,124 @@ int wave_context_kernel_stats(wave_context* ctx, int kind, int64_t* launches, do
   if (launches) *launches = l;
   if (total_ms) *total_ms = t;
   return WAVE_OK;
+}
+
+int wave_session_footprint(wave_context* ctx, const wave_geometry* geom, const wave_points* src,
+                           const wave_points* rec, int nt, int space_order, size_t* bytes_out) {
+  TRY(begin_call(ctx));
+  if (!bytes_out) return fail(ctx, WAVE_ERR_INVALID_ARG, "bytes_out is NULL");
+  Prob P;
+  TRY(prepare(ctx, geom, 1.0f, nt, space_order, &P));
+  wave_points empty{0, nullptr};
+  PointsHost hs, hr;
+  TRY(build_points_host(ctx, P, src ? src : &empty, &hs));
+  TRY(build_points_host(ctx, P, rec ? rec : &empty, &hr));
+  *bytes_out = session_bytes(P, hs, hr, std::max<long long>(hs.n, 1), std::max<long long>(hr.n, 1));
+  return WAVE_OK;
+}
+
+int wave_session_create(wave_context* ctx, wave_session** out, const wave_geometry* geom, const float* m,
+                        const wave_points* src, const float* q, const wave_points* rec, float dt, int nt,
+                        int space_order, int graph_chunk, void* stream) {
+  TRY(begin_call(ctx));
+  if (!out) return fail(ctx, WAVE_ERR_INVALID_ARG, "session pointer is NULL");
+  *out = nullptr;
+  if (graph_chunk < 0 || graph_chunk % 2) return fail(ctx, WAVE_ERR_INVALID_ARG, "graph_chunk must be even and >= 0");
+  DeviceGuard guard(ctx->device);
+  wave_session* S = new wave_session();
+  S->ctx = ctx;
+  S->stream = static_cast<cudaStream_t>(stream);
+  S->chunk = graph_chunk;
+  int rc = session_create_impl(ctx, S, geom, m, src, q, rec, dt, nt, space_order);
+  if (rc == WAVE_OK) {
+    cudaError_t e = cudaStreamSynchronize(S->stream);
+    if (e != cudaSuccess) rc = fail(ctx, WAVE_ERR_CUDA, "session set-up failed: %s", cudaGetErrorString(e));
+  }
+  if (rc != WAVE_OK) {
+    cudaStreamSynchronize(S->stream);
+    cudaGetLastError();
+    if (S->exec) cudaGraphExecDestroy(S->exec);
+    if (S->done) cudaEventDestroy(S->done);
+    sess_free(S);
+    delete S;
+    return rc;
+  }
+  *out = S;
+  return WAVE_OK;
+}
+
+int wave_session_advance(wave_session* S, int steps, int* steps_left) {
+  if (!S) return WAVE_ERR_INVALID_ARG;
+  wave_context* ctx = S->ctx;
+  DeviceGuard guard(ctx->device);
+  Prob& P = S->P;
+  const int total = P.nt - 1;
+  cudaStream_t s = S->stream;
+  while (steps > 0 && S->next < total) {
+    if (S->exec && S->next % S->chunk == 0 && total - S->next >= S->chunk) {
+      CK(cudaGraphLaunch(S->exec, s));
+      ctx->launches[WAVE_KERNEL_STEP] += S->chunk;
+      ctx->launches[WAVE_KERNEL_SPARSE] += 2 * S->chunk;
+      ctx->launches[WAVE_KERNEL_OTHER] += 1;
+      S->next += S->chunk;
+      steps -= S->chunk;
+    } else {
+      // steps that do not fill a whole captured chunk (the tail, or every
+      // step when no graph was captured) run as ordinary launches
+      const int stop = std::min(total, S->next + std::max(steps, 1));
+      TRY(forward_steps(ctx, P, S->W, S->next, stop, S->q, &S->src, S->d, S->nr > 0 ? &S->rec : nullptr, nullptr,
+                        0, 0, s));
+      steps -= stop - S->next;
+      S->next = stop;
+    }
+  }
+  if (S->next >= total) CK(cudaEventRecord(S->done, s));
+  if (steps_left) *steps_left = total - S->next;
+  return WAVE_OK;
+}
+
+int wave_session_query(wave_session* S, int* done) {
+  if (!S || !done) return WAVE_ERR_INVALID_ARG;
+  *done = 0;
+  if (S->next < S->P.nt - 1) return WAVE_OK;
+  cudaError_t e = cudaEventQuery(S->done);
+  if (e == cudaSuccess) *done = 1;
+  else if (e != cudaErrorNotReady) {
+    cudaGetLastError();
+    return fail(S->ctx, WAVE_ERR_CUDA, "session query failed: %s", cudaGetErrorString(e));
+  }
+  return WAVE_OK;
+}
+
+int wave_session_read(wave_session* S, float* d_out) {
+  if (!S) return WAVE_ERR_INVALID_ARG;
+  wave_context* ctx = S->ctx;
+  if (S->next < S->P.nt - 1) return fail(ctx, WAVE_ERR_INVALID_ARG, "session has steps left to enqueue");
+  DeviceGuard guard(ctx->device);
+  if (S->nr > 0 && !d_out) return fail(ctx, WAVE_ERR_INVALID_ARG, "output is NULL");
+  if (S->nr > 0)
+    CK(cudaMemcpyAsync(d_out, S->d, static_cast<size_t>(S->P.nt) * S->nr * 4, cudaMemcpyDefault, S->stream));
+  CK(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, S->stream));
+  CK(cudaStreamSynchronize(S->stream));
+  if (*ctx->h_status != kDevOk) return fail(ctx, WAVE_ERR_TIMEOUT, "a kernel gave up a bounded wait");
+  return WAVE_OK;
+}
+
+int wave_session_destroy(wave_session* S) {
+  if (!S) return WAVE_OK;
+  DeviceGuard guard(S->ctx->device);
+  cudaStreamSynchronize(S->stream);
+  if (S->exec) cudaGraphExecDestroy(S->exec);
+  if (S->done) cudaEventDestroy(S->done);
+  sess_free(S);
+  cudaGetLastError();
+  delete S;
+  return WAVE_OK;
+}
+
+size_t wave_context_budget_free(const wave_context* ctx) {
+  if (!ctx || !ctx->budget) return 0;
+  return ctx->budget > ctx->held ? ctx->budget - ctx->held : 0;
 }
 
 int wave_context_reset_stats(wave_context* ctx) {

@@ -181,5 +181,11 @@ cudaError_t launch_snapshot_store(const GridDims& g, const float* field, void* s
 cudaError_t launch_pack_state(const GridDims& g, const float* field, float* dense, cudaStream_t s);
 cudaError_t launch_unpack_state(const GridDims& g, const float* dense, float* field, cudaStream_t s);
 cudaError_t launch_fill_zero(float* p, long long n, cudaStream_t s);
+// graph-replay variants: time row = *counter + offset (+1 for the gather)
+cudaError_t launch_inject_counter(const InjectSet& is, const float* q, long long ns, const int* counter, int offset,
+                                  float* field, cudaStream_t s);
+cudaError_t launch_gather_counter(const GatherSet& gs, const float* field, float* d, const int* counter, int offset,
+                                  cudaStream_t s);
+cudaError_t launch_counter_add(int* counter, int delta, cudaStream_t s);
 
 }  // namespace wave

@@ -151,3 +151,56 @@ def smooth_perturbation(shape_xyz, spacing, seed, corr_len=30.0):
     """A smooth, bounded model perturbation (unit max-abs) for Taylor tests."""
     g = smooth_gaussian_noise(shape_xyz, corr_len / spacing[0], seed).astype(np.float64)
     return g / np.abs(g).max()
+
+
+def layered_profile(nz, dz, n_layers, v_min=1.5, v_max=4.5, perturb=0.05, seed=0):
+    """1D velocity v(z) (km/s, length nz): ``n_layers`` flat layers with sorted
+    velocities drawn in [v_min, v_max] (the top one v_min), interfaces at sorted
+    random depths, each layer scaled by 1 + U(-perturb, perturb), clipped."""
+    r = rng(seed)
+    depth = (nz - 1) * dz
+    vs = np.sort(r.uniform(v_min, v_max, size=n_layers))
+    vs[0] = v_min
+    vs = np.clip(vs * (1.0 + r.uniform(-perturb, perturb, size=n_layers)), v_min, v_max)
+    cuts = np.sort(r.uniform(0.05 * depth, 0.95 * depth, size=n_layers - 1))
+    z = np.arange(nz, dtype=np.float64) * dz
+    v = np.full(nz, vs[0])
+    for i, c in enumerate(cuts):
+        v = np.where(z >= c, vs[i + 1], v)
+    return v
+
+
+def serving_requests(n, seed=99):
+    """Seeded stream of shot-modelling requests: half 2D (N x N, N in
+    [201, 1001]), half 3D (N^3, N in [128, 320]); space order in {4, 8, 16};
+    nt in [500, 2000]; 3-8 velocity layers in [1.5, 4.5] km/s; one 10 Hz
+    Ricker source at the surface centre; 100-1000 surface receivers;
+    h = 10 m, 20-point (2D) or 40-point (3D) absorbing layer."""
+    r = rng(seed)
+    out = []
+    for i in range(n):
+        ndim = 2 if r.uniform() < 0.5 else 3
+        N = int(r.integers(201, 1002)) if ndim == 2 else int(r.integers(128, 321))
+        out.append(dict(id=i, ndim=ndim, N=N, h=10.0, nbl=20 if ndim == 2 else 40,
+                        so=int(r.choice([4, 8, 16])), nt=int(r.integers(500, 2001)),
+                        n_layers=int(r.integers(3, 9)), n_rec=int(r.integers(100, 1001)),
+                        model_seed=int(seed * 100003 + i), f0=0.010))
+    return out
+
+
+def request_points(req):
+    """Source (surface centre, 20 m deep) and receivers (surface line in 2D, a
+    k x k surface grid with k*k >= n_rec in 3D, at 20 m) of a serving request."""
+    N, h, nd = req["N"], req["h"], req["ndim"]
+    ext = (N - 1) * h
+    if nd == 2:
+        src = np.array([[0.5 * ext, 20.0]], dtype=np.float32)
+        x = np.linspace(0.0, ext, req["n_rec"])
+        rec = np.stack([x, np.full_like(x, 20.0)], axis=1).astype(np.float32)
+    else:
+        src = np.array([[0.5 * ext, 0.5 * ext, 20.0]], dtype=np.float32)
+        k = int(np.ceil(np.sqrt(req["n_rec"])))
+        g = np.linspace(0.0, ext, k)
+        X, Y = np.meshgrid(g, g, indexing="xy")
+        rec = np.stack([X.ravel(), Y.ravel(), np.full(X.size, 20.0)], axis=1).astype(np.float32)
+    return src, rec

@@ -1,0 +1,144 @@
+"""Continuous-batching server for shot-modelling requests.
+
+Requests (forward modelling of one shot: geometry, layered model, space
+order, nt) arrive over time.  A single host scheduler thread:
+
+  * admits waiting requests in arrival order while a stream slot is free and
+    the request's device footprint (wave_session_footprint) fits the HBM
+    budget left in the context (wave_context_budget_free);
+  * creates a resident session on the slot's CUDA stream and enqueues all of
+    its time steps at once -- whole chunks as replays of the session's
+    captured CUDA graph -- so that the GPU interleaves the kernels of every
+    resident request;
+  * polls completion, copies the receiver data back, destroys the session
+    (freeing its memory for the next admissions) and records the latency.
+
+Every step of every request runs in the CUDA library; this module only
+schedules.  Results are identical to running each request alone.
+"""
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import inputs, wave
+
+
+@dataclass
+class Result:
+    req_id: int
+    data: np.ndarray
+    arrival: float
+    admitted: float
+    finished: float
+
+    @property
+    def latency(self):
+        return self.finished - self.arrival
+
+
+@dataclass
+class ServeStats:
+    results: dict = field(default_factory=dict)
+    wall: float = 0.0
+    max_resident: int = 0
+    peak_bytes: int = 0
+
+    def summary(self):
+        lat = np.array([r.latency for r in self.results.values()])
+        n = len(lat)
+        return {"requests": n, "shots_per_s": n / self.wall if self.wall > 0 else None,
+                "p50_latency_s": float(np.percentile(lat, 50)) if n else None,
+                "p99_latency_s": float(np.percentile(lat, 99)) if n else None,
+                "mean_latency_s": float(lat.mean()) if n else None, "wall_s": self.wall,
+                "max_resident": self.max_resident, "peak_workspace_bytes": self.peak_bytes}
+
+
+def request_problem(req, device):
+    """Materialise a request from ``inputs.serving_requests``: geometry, model
+    (broadcast on the device from its 1D profile), points, Ricker traces, dt."""
+    import torch
+    N, h, nd = req["N"], req["h"], req["ndim"]
+    shape = (N,) * nd
+    geom = wave.Geometry(shape=shape, spacing=(h,) * nd, nbl=req["nbl"], sponge_vref=4.5)
+    v = inputs.layered_profile(N, h, req["n_layers"], seed=req["model_seed"])
+    m1 = torch.from_numpy((1.0 / v ** 2).astype(np.float32)).to(device)
+    m = m1.view((N,) + (1,) * (nd - 1)).expand((N,) * nd).contiguous()
+    vmax = float(v.max())
+    dt = 0.4 * wave.wave_dt_max((h,) * nd, req["so"], vmax)
+    src, rec = inputs.request_points(req)
+    q = wave.wave_ricker(req["nt"], dt, req["f0"]).reshape(-1, 1)
+    return geom, m, src, q, rec, dt
+
+
+class ShotServer:
+    def __init__(self, device=0, hbm_budget_bytes=0, max_resident=32, graph_chunk=32):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.ctx = wave.Context(device, hbm_budget_bytes)
+        self.budget = int(hbm_budget_bytes)
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(max_resident)]
+        self.graph_chunk = graph_chunk
+
+    def close(self):
+        self.ctx.close()
+
+    def run(self, requests, arrivals, problem=request_problem):
+        """Serve ``requests`` arriving at ``arrivals`` (seconds from start)."""
+        order = np.argsort(arrivals, kind="stable")
+        pending = collections.deque((requests[i], float(arrivals[i])) for i in order)
+        waiting = collections.deque()
+        free_slots = list(range(len(self.streams)))
+        active = []
+        stats = ServeStats()
+        t0 = time.perf_counter()
+        while pending or waiting or active:
+            now = time.perf_counter() - t0
+            while pending and pending[0][1] <= now:
+                waiting.append(pending.popleft())
+            progressed = False
+            # admission in arrival order by slot and footprint
+            while waiting and free_slots:
+                req, arr = waiting[0]
+                geom, m, src, q, rec, dt = problem(req, self.device)
+                fp = wave.wave_session_footprint(self.ctx, geom, src, rec, req["nt"], req["so"])
+                if self.budget and fp > self.ctx.budget_free():
+                    if not active:
+                        raise RuntimeError("request %d needs %d bytes, more than the whole budget" % (req["id"], fp))
+                    break
+                waiting.popleft()
+                slot = free_slots.pop()
+                stream = self.streams[slot]
+                sess = wave.Session(self.ctx, geom, m, src, q, rec, dt, req["nt"], req["so"],
+                                    stream=wave.ctypes.c_void_p(stream.cuda_stream), graph_chunk=self.graph_chunk)
+                sess.advance(req["nt"])
+                active.append((req, arr, time.perf_counter() - t0, sess, slot))
+                stats.max_resident = max(stats.max_resident, len(active))
+                stats.peak_bytes = max(stats.peak_bytes, self.ctx.workspace_bytes())
+                progressed = True
+            # completion
+            still = []
+            for req, arr, adm, sess, slot in active:
+                if sess.done():
+                    data = sess.read()
+                    sess.close()
+                    free_slots.append(slot)
+                    stats.results[req["id"]] = Result(req["id"], data, arr, adm, time.perf_counter() - t0)
+                    progressed = True
+                else:
+                    still.append((req, arr, adm, sess, slot))
+            active = still
+            if not progressed:
+                nxt = pending[0][1] - (time.perf_counter() - t0) if pending and not waiting and not active else 0
+                time.sleep(min(max(nxt, 0.0), 0.01) if nxt > 0 else 0.0002)
+        stats.wall = time.perf_counter() - t0
+        return stats
+
+
+def poisson_arrivals(n, rate, seed=99):
+    """Arrival times of a Poisson process of the given rate (requests/s)."""
+    r = inputs.rng(seed + 7)
+    return np.cumsum(r.exponential(1.0 / rate, size=n)) - 0.0

@@ -84,6 +84,15 @@ _SIGS = {
                                                  ctypes.POINTER(ctypes.c_double)]),
     "wave_context_reset_stats": (ctypes.c_int, [_P]),
     "wave_objective_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), _P]),
+    "wave_session_footprint": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_size_t)]),
+    "wave_session_create": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_void_p), _P, _P, _P, _P, _P, ctypes.c_float,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+    "wave_session_advance": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "wave_session_query": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "wave_session_read": (ctypes.c_int, [_P, _P]),
+    "wave_session_destroy": (ctypes.c_int, [_P]),
+    "wave_context_budget_free": (ctypes.c_size_t, [_P]),
 }
 
 _lib = None
@@ -267,6 +276,70 @@ class Context:
 
     def reset_stats(self):
         _check(self, lib().wave_context_reset_stats(self.handle))
+
+    def budget_free(self):
+        return int(lib().wave_context_budget_free(self.handle))
+
+
+class Session:
+    """A resident forward-modelling request (wave_session_*): created on a
+    stream, advanced asynchronously, polled, read, destroyed."""
+
+    def __init__(self, ctx, geom, m, src, q, rec, dt, nt, space_order, stream=None, graph_chunk=32):
+        self.ctx = ctx
+        self.nt = int(nt)
+        g = geom.to_c()
+        ps, self._src = _points(src, geom.ndim)
+        pr, self._rec = _points(rec, geom.ndim)
+        self.n_rec = int(pr.n)
+        m = _f32(m)
+        q = _f32(q) if ps.n else None
+        h = ctypes.c_void_p()
+        st = stream if stream is not None else _stream_for(m, q)
+        rc = lib().wave_session_create(ctx.handle, ctypes.byref(h), ctypes.byref(g), _ptr(m), ctypes.byref(ps),
+                                       _ptr(q), ctypes.byref(pr), ctypes.c_float(dt), self.nt, int(space_order),
+                                       int(graph_chunk), st)
+        _check(ctx, rc)
+        self.handle = h
+        self.steps_left = self.nt - 1
+
+    def advance(self, steps):
+        left = ctypes.c_int()
+        _check(self.ctx, lib().wave_session_advance(self.handle, int(steps), ctypes.byref(left)))
+        self.steps_left = left.value
+        return self.steps_left
+
+    def done(self):
+        d = ctypes.c_int()
+        _check(self.ctx, lib().wave_session_query(self.handle, ctypes.byref(d)))
+        return bool(d.value)
+
+    def read(self, out=None):
+        if out is None:
+            out = np.empty((self.nt, self.n_rec), dtype=np.float32)
+        _check(self.ctx, lib().wave_session_read(self.handle, _ptr(out) if self.n_rec else None))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().wave_session_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+def wave_session_footprint(ctx, geom, src, rec, nt, space_order):
+    g = geom.to_c()
+    ps, _s = _points(src, geom.ndim)
+    pr, _r = _points(rec, geom.ndim)
+    b = ctypes.c_size_t()
+    _check(ctx, lib().wave_session_footprint(ctx.handle, ctypes.byref(g), ctypes.byref(ps), ctypes.byref(pr),
+                                             int(nt), int(space_order), ctypes.byref(b)))
+    return int(b.value)
 
 
 # ---------------------------------------------------------------------------
