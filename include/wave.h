@@ -99,8 +99,13 @@ typedef struct {
 
 /* Storage of the forward wavefield for the imaging condition of Eq. 3.
  * FULL_*: every time level u^1..u^{nt-1} is kept (Sec. IV-B4 "save" flag).
- * CHECKPOINT_*: only exact FP32 checkpoints (u^{k-1}, u^k) every S steps are
- * kept; each segment is recomputed before its adjoint sweep.
+ * CHECKPOINT_*: a buffer of F levels (as many as fit the budget / free memory,
+ * or the interval set with wave_context_set_checkpoint_interval) first holds
+ * the last F levels, stored during the forward sweep; the earlier levels are
+ * recomputed segment by segment from exact FP32 checkpoints (u^{k-1}, u^k)
+ * into the same buffer once the adjoint sweep has consumed the tail.
+ * Recomputation is deterministic: every mode gives the same gradient as the
+ * FULL mode of the same format, bit for bit.
  * *_BF16 / *_FP16: snapshots are stored in 16 bits with one power-of-two
  * scale per slab of 64 (x) by 2 (axis 1) points of one plane; all stencil
  * arithmetic and gradient accumulation stay FP32.

@@ -88,15 +88,18 @@ __device__ __forceinline__ float4 load_snap4_smem(const unsigned char* p, float 
 }
 
 // Resident CTAs per SM requested from the register allocator: 3 up to radius
-// 4 (72 registers), 2 for radius 5-6 (<= 113 registers); radius 7-8 are held
-// to one CTA per SM by their shared-memory ring anyway.
+// 4, 2 above (the lead-plane ring keeps the shared memory of radius 7-8
+// within two CTAs per SM).
 #ifndef WAVE_STEP_MINB
 #define WAVE_STEP_MINB 3
+#endif
+#ifndef WAVE_STEP_MINB_HI
+#define WAVE_STEP_MINB_HI 2
 #endif
 
 
 template <int R, int NDIM, int MODE>
-__global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_STEP_MINB : (R <= 6 ? 2 : 1)))
+__global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_STEP_MINB : WAVE_STEP_MINB_HI))
     step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
                 const __grid_constant__ CUtensorMap tm_cm, const __grid_constant__ CUtensorMap tm_g,
                 const __grid_constant__ CUtensorMap tm_s, const StepParams p) {
@@ -157,8 +160,11 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
         const int slot = s % T::NSU;
         if (s >= T::NSU) ok = mbar_wait_bounded(&emptyU[slot], ((s / T::NSU) - 1) & 1, abort_flag, kWaitLimitNs);
         if (!ok) break;
-        mbar_arrive_expect_tx(&fullU[slot], T::U_BYTES);
-        tma_load_4d(Ubase + slot * (T::U_STRIDE / 4), &tm_u, x0 - T::HX, y0 - R, z0 - RZ + s, p.cur, &fullU[slot]);
+        mbar_arrive_expect_tx(&fullU[slot], T::Q_BYTES);
+        if constexpr (T::LEAD)
+          tma_load_4d(Ubase + slot * (T::Q_STRIDE / 4), &tm_p, x0, y0, z0 - RZ + s, p.cur, &fullU[slot]);
+        else
+          tma_load_4d(Ubase + slot * (T::Q_STRIDE / 4), &tm_u, x0 - T::HX, y0 - R, z0 - RZ + s, p.cur, &fullU[slot]);
         issuedU = s + 1;
         if (s >= 2 * RZ) {
           const int j = s - 2 * RZ;
@@ -166,7 +172,9 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
           if (j >= T::NSP) ok = mbar_wait_bounded(&emptyP[ps], ((j / T::NSP) - 1) & 1, abort_flag, kWaitLimitNs);
           if (!ok) break;
           unsigned char* pd = Pbase + ps * L::P_BYTES;
-          mbar_arrive_expect_tx(&fullP[ps], L::P_BYTES);
+          mbar_arrive_expect_tx(&fullP[ps], L::P_TX);
+          if constexpr (T::LEAD)
+            tma_load_4d(pd + L::HALO_OFF, &tm_u, x0 - T::HX, y0 - R, z0 + j, p.cur, &fullP[ps]);
           tma_load_4d(pd + L::PREV_OFF, &tm_p, x0, y0, z0 + j, p.prev, &fullP[ps]);
           tma_load_3d(pd + L::CM_OFF, &tm_cm, x0, y0, z0 + j, &fullP[ps]);
           if (mode_is_grad(MODE)) {
@@ -205,8 +213,9 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
   const int gx = x0 + 4 * tx;
   const int gy = y0 + ty;
   const bool store_ok = (gx < p.NX) && (gy < p.NY);
-  const int lofs = (R + ty) * T::UW + T::HX + 4 * tx;  // centre of this quad in a U stage
+  const int lofs = (R + ty) * T::UW + T::HX + 4 * tx;  // centre of this quad in a halo box
   const int tofs = (ty * T::BX + 4 * tx) * 4;          // byte offset of this quad in a tile
+  const int qofs = T::LEAD ? tofs / 4 : lofs;           // this quad in a queue-feed stage
 
   // sponge along x (per point) and axis 1 (per row)
   const float ey = sponge_term(gy, p.NY, p.nbly, p.emy);
@@ -216,16 +225,30 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
   // all terms are >= 0: the column is undamped iff the largest is zero
   const float exy_max = fmaxf(fmaxf(exy[0], exy[1]), fmaxf(exy[2], exy[3]));
 
-  // coefficients as packed pairs (loop invariant)
+  // Coefficients as packed pairs (loop invariant) up to radius 6; above, the
+  // 6R pairs would cost too many registers, so the multiply takes the scalar
+  // coefficient from the constant bank and only the sums stay packed.
+  constexpr bool PCOEF = R <= 6;
+  constexpr int NPC = PCOEF ? R : 1;
   const float2 c0v = make_float2(p.c0, p.c0);
-  float2 cxv[R], cyv[R], czv[RZ > 0 ? RZ : 1];
+  float2 cxv[NPC], cyv[NPC], czv[PCOEF && RZ > 0 ? RZ : 1];
 #pragma unroll
-  for (int k = 0; k < R; ++k) {
+  for (int k = 0; k < NPC; ++k) {
     cxv[k] = make_float2(p.cx[k], p.cx[k]);
     cyv[k] = make_float2(p.cy[k], p.cy[k]);
   }
 #pragma unroll
-  for (int k = 0; k < RZ; ++k) czv[k] = make_float2(p.cz[k], p.cz[k]);
+  for (int k = 0; k < (PCOEF ? RZ : 0); ++k) czv[k] = make_float2(p.cz[k], p.cz[k]);
+  // acc += c * (a + b) on a packed pair
+  auto tap2 = [&](float2& acc, const float2& cv, float cs, const float2& a, const float2& b) {
+    const float2 sum = __fadd2_rn(a, b);
+    if constexpr (PCOEF) {
+      acc = __ffma2_rn(cv, sum, acc);
+    } else {
+      acc.x = fmaf(cs, sum.x, acc.x);
+      acc.y = fmaf(cs, sum.y, acc.y);
+    }
+  };
 
   // Register queue of the centre level along the streamed axis: before output
   // plane z, q[0 .. 2RZ-1] hold planes z-RZ .. z+RZ-1; plane z+RZ lands in
@@ -242,8 +265,8 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
     ok = mbar_wait_bounded(&fullU[slot], (s / T::NSU) & 1, abort_flag, kWaitLimitNs);
     ok = __all_sync(0xffffffffu, ok);
     if (!ok) break;
-    q[s] = lds4(Ubase + slot * (T::U_STRIDE / 4) + lofs);
-    if (s < RZ) {
+    q[s] = lds4(Ubase + slot * (T::Q_STRIDE / 4) + qofs);
+    if (T::LEAD || s < RZ) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&emptyU[slot]);
     }
@@ -262,9 +285,20 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
     const int uc = sc % T::NSU;
     bool good = mbar_wait_bounded(&fullU[un], (sn / T::NSU) & 1, abort_flag, kWaitLimitNs);
     if (!__all_sync(0xffffffffu, good)) return false;
-    q[2 * RZ] = lds4(Ubase + un * (T::U_STRIDE / 4) + lofs);
+    q[2 * RZ] = lds4(Ubase + un * (T::Q_STRIDE / 4) + qofs);
+    if constexpr (T::LEAD) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&emptyU[un]);
+    }
     const float4 c = q[RZ];
-    const float* Uc = Ubase + uc * (T::U_STRIDE / 4) + lofs;
+    const int ps = j % T::NSP;
+    if constexpr (T::LEAD) {
+      // the centre halo box arrives with the per-point tiles
+      good = mbar_wait_bounded(&fullP[ps], (j / T::NSP) & 1, abort_flag, kWaitLimitNs);
+      if (!__all_sync(0xffffffffu, good)) return false;
+    }
+    const float* Uc = T::LEAD ? reinterpret_cast<const float*>(Pbase + ps * L::P_BYTES + L::HALO_OFF) + lofs
+                              : Ubase + uc * (T::Q_STRIDE / 4) + lofs;
 
     // Laplacian on two packed pairs (points 0,1 and 2,3 of the quad)
     float2 la = __fmul2_rn(c0v, make_float2(c.x, c.y));
@@ -273,15 +307,15 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
     for (int k = 1; k <= RZ; ++k) {
       const float4 a = q[RZ - k];
       const float4 b = q[RZ + k];
-      la = __ffma2_rn(czv[k - 1], __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y)), la);
-      lb = __ffma2_rn(czv[k - 1], __fadd2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w)), lb);
+      tap2(la, czv[PCOEF ? k - 1 : 0], p.cz[k - 1], make_float2(a.x, a.y), make_float2(b.x, b.y));
+      tap2(lb, czv[PCOEF ? k - 1 : 0], p.cz[k - 1], make_float2(a.z, a.w), make_float2(b.z, b.w));
     }
 #pragma unroll
     for (int k = 1; k <= R; ++k) {
       const float4 a = lds4(Uc - k * T::UW);
       const float4 b = lds4(Uc + k * T::UW);
-      la = __ffma2_rn(cyv[k - 1], __fadd2_rn(make_float2(a.x, a.y), make_float2(b.x, b.y)), la);
-      lb = __ffma2_rn(cyv[k - 1], __fadd2_rn(make_float2(a.z, a.w), make_float2(b.z, b.w)), lb);
+      tap2(la, cyv[PCOEF ? k - 1 : 0], p.cy[k - 1], make_float2(a.x, a.y), make_float2(b.x, b.y));
+      tap2(lb, cyv[PCOEF ? k - 1 : 0], p.cy[k - 1], make_float2(a.z, a.w), make_float2(b.z, b.w));
     }
     {
       constexpr int NH = T::HX / 4;  // halo quads per side
@@ -308,8 +342,10 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
         constexpr int H = T::HX;
         if (k % 2 == 0) {
           // even offsets keep the pairs register-aligned
-          la = __ffma2_rn(cxv[k - 1], __fadd2_rn(make_float2(v[H - k], v[H + 1 - k]), make_float2(v[H + k], v[H + 1 + k])), la);
-          lb = __ffma2_rn(cxv[k - 1], __fadd2_rn(make_float2(v[H + 2 - k], v[H + 3 - k]), make_float2(v[H + 2 + k], v[H + 3 + k])), lb);
+          tap2(la, cxv[PCOEF ? k - 1 : 0], p.cx[k - 1], make_float2(v[H - k], v[H + 1 - k]),
+               make_float2(v[H + k], v[H + 1 + k]));
+          tap2(lb, cxv[PCOEF ? k - 1 : 0], p.cx[k - 1], make_float2(v[H + 2 - k], v[H + 3 - k]),
+               make_float2(v[H + 2 + k], v[H + 3 + k]));
         } else {
           la.x = fmaf(p.cx[k - 1], v[H + 0 - k] + v[H + 0 + k], la.x);
           la.y = fmaf(p.cx[k - 1], v[H + 1 - k] + v[H + 1 + k], la.y);
@@ -320,9 +356,10 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
     }
     const float4 lap = make_float4(la.x, la.y, lb.x, lb.y);
 
-    const int ps = j % T::NSP;
-    good = mbar_wait_bounded(&fullP[ps], (j / T::NSP) & 1, abort_flag, kWaitLimitNs);
-    if (!__all_sync(0xffffffffu, good)) return false;
+    if constexpr (!T::LEAD) {
+      good = mbar_wait_bounded(&fullP[ps], (j / T::NSP) & 1, abort_flag, kWaitLimitNs);
+      if (!__all_sync(0xffffffffu, good)) return false;
+    }
     const unsigned char* Pst = Pbase + ps * L::P_BYTES;
     const float4 prev = *reinterpret_cast<const float4*>(Pst + L::PREV_OFF + tofs);
     const float4 cm = *reinterpret_cast<const float4*>(Pst + L::CM_OFF + tofs);
@@ -379,7 +416,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
 
     __syncwarp();
     if (lane == 0) {
-      mbar_arrive(&emptyU[uc]);
+      if constexpr (!T::LEAD) mbar_arrive(&emptyU[uc]);
       mbar_arrive(&emptyP[ps]);
     }
     return true;

@@ -538,27 +538,35 @@ struct PointsHost {
   std::vector<float> wts;
 };
 
-int build_points_host(wave_context* ctx, Prob& P, const wave_points* pts, PointsHost* H) {
+// Coordinates of a point set on the host, and its cache key (coordinates and
+// geometry).
+int read_points(wave_context* ctx, Prob& P, const wave_points* pts, std::vector<float>* c, uint64_t* key_out) {
   if (!pts) return fail(ctx, WAVE_ERR_INVALID_ARG, "point set is NULL");
   const long long n = pts->n;
   if (n < 0 || n > (1LL << 28)) return fail(ctx, WAVE_ERR_INVALID_ARG, "point count %lld out of range", n);
   if (n > 0 && !pts->coords) return fail(ctx, WAVE_ERR_INVALID_ARG, "point coordinates are NULL");
-  const int nd = P.ndim;
-  std::vector<float> c(static_cast<size_t>(n) * nd);
+  c->resize(static_cast<size_t>(n) * P.ndim);
   if (n > 0) {
     bool dev = false;
     TRY(classify(ctx, pts->coords, &dev));
-    if (dev) CK(cudaMemcpy(c.data(), pts->coords, c.size() * sizeof(float), cudaMemcpyDeviceToHost));
-    else std::memcpy(c.data(), pts->coords, c.size() * sizeof(float));
+    if (dev) CK(cudaMemcpy(c->data(), pts->coords, c->size() * sizeof(float), cudaMemcpyDeviceToHost));
+    else std::memcpy(c->data(), pts->coords, c->size() * sizeof(float));
   }
   uint64_t key = 1469598103934665603ull;
-  key = fnv(key, c.data(), c.size() * sizeof(float));
+  key = fnv(key, c->data(), c->size() * sizeof(float));
   key = fnv(key, &n, sizeof(n));
   key = fnv(key, &P.g, sizeof(P.g));
   key = fnv(key, P.h, sizeof(P.h));
   key = fnv(key, P.o, sizeof(P.o));
   key = fnv(key, P.lo, sizeof(P.lo));
   key = fnv(key, P.hi, sizeof(P.hi));
+  *key_out = key;
+  return WAVE_OK;
+}
+
+int build_points_from(wave_context* ctx, Prob& P, const std::vector<float>& c, uint64_t key, PointsHost* H) {
+  const int nd = P.ndim;
+  const long long n = static_cast<long long>(c.size() / nd);
   H->n = n;
   H->key = key;
   const GridDims& g = P.g;
@@ -623,6 +631,13 @@ int build_points_host(wave_context* ctx, Prob& P, const wave_points* pts, Points
   return WAVE_OK;
 }
 
+int build_points_host(wave_context* ctx, Prob& P, const wave_points* pts, PointsHost* H) {
+  std::vector<float> c;
+  uint64_t key = 0;
+  TRY(read_points(ctx, P, pts, &c, &key));
+  return build_points_from(ctx, P, c, key, H);
+}
+
 // Device bytes of the uploaded structures of a point set (each array rounded
 // like a workspace allocation).
 size_t points_device_bytes(const PointsHost& H) {
@@ -654,14 +669,18 @@ int upload_points(wave_context* ctx, const PointsHost& H, PointSetDev& e, cudaSt
 // Point structures for one call, cached in the context (keyed by coordinates
 // and geometry) so repeated calls with the same points skip the build.
 int prepare_points(wave_context* ctx, Prob& P, const wave_points* pts, cudaStream_t s, PointSetDev** out) {
-  PointsHost H;
-  TRY(build_points_host(ctx, P, pts, &H));
+  std::vector<float> c;
+  uint64_t key = 0;
+  TRY(read_points(ctx, P, pts, &c, &key));
+  const long long n = pts->n;
   for (auto& e : ctx->pts) {
-    if (e.valid && e.key == H.key && e.n == H.n) {
+    if (e.valid && e.key == key && e.n == n) {
       *out = &e;
       return WAVE_OK;
     }
   }
+  PointsHost H;
+  TRY(build_points_from(ctx, P, c, key, &H));
   PointSetDev& e = ctx->pts[ctx->pts_next];
   ctx->pts_next = (ctx->pts_next + 1) % 4;
   e.valid = false;
@@ -953,11 +972,25 @@ int adjoint_impl(wave_context* ctx, const wave_geometry* geom, const float* m, c
 }
 
 // ---------------------------------------------------------------- gradient
-int choose_storage(wave_context* ctx, Prob& P, int mode, int* fmt, bool* ckpt, int* interval) {
+// Storage plan for the forward wavefield of Eq. 3.  A buffer of F snapshot
+// levels first holds the last F levels (nt-F .. nt-1), stored during the
+// forward sweep; the earlier levels are recomputed from exact FP32
+// checkpoints in segments of S <= F levels, reusing the same buffer once the
+// adjoint sweep has consumed the stored tail.  F = nt-1 is full storage (no
+// checkpoints); F = S is pure checkpointing.
+struct StoragePlan {
+  int fmt = 0;   // 0 FP32, 1 BF16, 2 FP16
+  int F = 0;     // levels in the snapshot buffer
+  int S = 0;     // segment length of the recomputed part
+  int T0 = 1;    // first stored level of the tail
+  int nseg = 0;  // recomputed segments covering levels [0, T0)
+};
+
+int plan_storage(wave_context* ctx, Prob& P, int mode, StoragePlan* plan) {
   if (mode < WAVE_SNAP_FULL_FP32 || mode > WAVE_SNAP_AUTO) return fail(ctx, WAVE_ERR_INVALID_ARG, "bad snap_mode %d", mode);
   const int nt = P.nt;
   const size_t fb = static_cast<size_t>(P.slot_elems) * 4;
-  auto snap_bytes = [&](int f) {
+  auto level_bytes = [&](int f) {
     return static_cast<size_t>(P.slot_elems) * (f == 0 ? 4 : 2) + (f == 0 ? 0 : static_cast<size_t>(P.scale_elems) * 4);
   };
   size_t avail;
@@ -975,32 +1008,38 @@ int choose_storage(wave_context* ctx, Prob& P, int mode, int* fmt, bool* ckpt, i
     avail = static_cast<size_t>(avail * 0.92);
   }
   int f = 0;
-  bool c = false;
+  bool ckpt = false;
   switch (mode) {
     case WAVE_SNAP_FULL_FP32: f = 0; break;
     case WAVE_SNAP_FULL_BF16: f = 1; break;
     case WAVE_SNAP_FULL_FP16: f = 2; break;
-    case WAVE_SNAP_CHECKPOINT_FP32: f = 0; c = true; break;
-    case WAVE_SNAP_CHECKPOINT_BF16: f = 1; c = true; break;
-    case WAVE_SNAP_CHECKPOINT_FP16: f = 2; c = true; break;
-    case WAVE_SNAP_AUTO: f = 0; c = snap_bytes(0) * static_cast<size_t>(nt) > avail; break;
+    case WAVE_SNAP_CHECKPOINT_FP32: f = 0; ckpt = true; break;
+    case WAVE_SNAP_CHECKPOINT_BF16: f = 1; ckpt = true; break;
+    case WAVE_SNAP_CHECKPOINT_FP16: f = 2; ckpt = true; break;
+    case WAVE_SNAP_AUTO: f = 0; ckpt = level_bytes(0) * static_cast<size_t>(nt - 1) > avail; break;
   }
-  *fmt = f;
-  *ckpt = c;
-  *interval = nt;
-  if (c) {
-    int S = ctx->ckpt_interval;
-    if (S <= 0) {
-      const double sb = static_cast<double>(snap_bytes(f));
-      S = static_cast<int>(std::ceil(std::sqrt(2.0 * fb * nt / sb)));
-      // fewer, longer segments when memory allows (fewer checkpoint copies)
-      while (S < nt && (static_cast<size_t>(2 * S) * snap_bytes(f) +
-                        static_cast<size_t>((nt + 2 * S - 1) / (2 * S)) * 2 * fb) <= avail / 2)
-        S *= 2;
-      S = std::max(1, std::min(S, nt));
+  const size_t lb = level_bytes(f);
+  int F = nt - 1;
+  if (ckpt) {
+    if (ctx->ckpt_interval > 0) {
+      F = std::min(ctx->ckpt_interval, nt - 1);
+    } else {
+      // largest buffer such that the buffer plus the checkpoints fit
+      F = static_cast<int>(std::min<size_t>(avail / lb, static_cast<size_t>(nt - 1)));
+      while (F > 1) {
+        const int T0 = nt - F;
+        const size_t nseg = static_cast<size_t>((T0 + F - 1) / F);
+        if (static_cast<size_t>(F) * lb + nseg * 2 * fb <= avail) break;
+        --F;
+      }
+      F = std::max(F, 1);
     }
-    *interval = S;
   }
+  plan->fmt = f;
+  plan->F = F;
+  plan->S = F;
+  plan->T0 = nt - F;
+  plan->nseg = plan->T0 > 1 ? (plan->T0 + F - 1) / F : 0;
   return WAVE_OK;
 }
 
@@ -1015,10 +1054,8 @@ int gradient_impl(wave_context* ctx, const wave_geometry* geom, const float* m, 
   const long long ns = src ? src->n : 0, nr = rec ? rec->n : 0;
   if (ns > 0 && !q) return fail(ctx, WAVE_ERR_INVALID_ARG, "source traces are NULL");
   if (nr > 0 && !d_obs && !y_given) return fail(ctx, WAVE_ERR_INVALID_ARG, "observed data are NULL");
-  int fmt;
-  bool ckpt;
-  int S;
-  TRY(choose_storage(ctx, P, snap_mode, &fmt, &ckpt, &S));
+  StoragePlan plan;
+  TRY(plan_storage(ctx, P, snap_mode, &plan));
   const void* mdev;
   TRY(stage_in(ctx, "m", m, P.phys_elems * 4, s, &mdev));
   const void* qdev = nullptr;
@@ -1048,39 +1085,35 @@ int gradient_impl(wave_context* ctx, const wave_geometry* geom, const float* m, 
     r = rout.dev ? static_cast<float*>(rout.dev) : static_cast<float*>(p);
   }
   const float* qd = static_cast<const float*>(qdev);
-  // storage
+  // storage: a buffer of plan.F levels; checkpoints at the segment starts
   SnapStore SS;
-  const int levels = ckpt ? S : nt - 1;
-  const int nseg = ckpt ? (nt + S - 1) / S : 1;
+  const int T0 = plan.T0, S = plan.S, nseg = plan.nseg;
   float* ck = nullptr;
-  if (ckpt) {
+  if (nseg > 0) {
     TRY(ws_get(ctx, "ckpt", static_cast<size_t>(nseg) * 2 * P.slot_elems * 4, &p));
     ck = static_cast<float*>(p);
   }
-  TRY(alloc_snapshots(ctx, P, fmt, levels, &SS));
+  TRY(alloc_snapshots(ctx, P, plan.fmt, plan.F, &SS));
   W.maps.s = SS.map;
-  // forward sweep
+  // forward sweep: checkpoints before each segment start, the tail stored
   CK(cudaMemsetAsync(slot_ptr(W, P, 0), 0, 2 * P.slot_elems * 4, s));
   CK(cudaMemsetAsync(W.grad, 0, P.slot_elems * 4, s));
   if (nr > 0) {
     GatherSet grec = gather_set(P, Rr);
     TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_gather(grec, slot_ptr(W, P, fslot(0)), d, s); }));
   }
-  if (!ckpt) {
-    // full storage: level j stored at index j-1, j = 1..nt-1
-    TRY(forward_steps(ctx, P, W, 0, nt - 1, qd, Sp, d, Rr, &SS, 1, 1, s));
-    TRY(store_level(ctx, P, W, fslot(nt - 1), &SS, nt - 2, s));
-  } else {
-    for (int seg = 0; seg < nseg; ++seg) {
-      const int L0 = seg * S;
-      // checkpoint (u^{L0-1}, u^{L0})
-      float* c0 = ck + static_cast<long long>(seg) * 2 * P.slot_elems;
-      CK(cudaMemcpyAsync(c0, slot_ptr(W, P, fslot(L0 - 1)), P.slot_elems * 4, cudaMemcpyDeviceToDevice, s));
-      CK(cudaMemcpyAsync(c0 + P.slot_elems, slot_ptr(W, P, fslot(L0)), P.slot_elems * 4, cudaMemcpyDeviceToDevice, s));
-      const int L1 = std::min(L0 + S, nt);
-      TRY(forward_steps(ctx, P, W, L0, std::min(L1, nt - 1), qd, Sp, d, Rr, nullptr, 0, 0, s));
-    }
+  for (int seg = 0; seg < nseg; ++seg) {
+    const int L0 = seg * S;
+    const int L1 = std::min(L0 + S, T0);
+    float* c0 = ck + static_cast<long long>(seg) * 2 * P.slot_elems;
+    CK(cudaMemcpyAsync(c0, slot_ptr(W, P, fslot(L0 - 1)), P.slot_elems * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(c0 + P.slot_elems, slot_ptr(W, P, fslot(L0)), P.slot_elems * 4, cudaMemcpyDeviceToDevice, s));
+    TRY(forward_steps(ctx, P, W, L0, L1, qd, Sp, d, Rr, nullptr, 0, 0, s));
   }
+  // steps n >= first computed step store the centre level n >= T0 at index n - T0
+  const int n_first = nseg > 0 ? std::min(nseg * S, T0) : 0;
+  TRY(forward_steps(ctx, P, W, n_first, nt - 1, qd, Sp, d, Rr, &SS, T0, T0, s));
+  TRY(store_level(ctx, P, W, fslot(nt - 1), &SS, nt - 1 - T0, s));
   // residual and objective
   if (nr > 0 && !y_given) {
     const long long n = static_cast<long long>(nt) * nr;
@@ -1093,23 +1126,20 @@ int gradient_impl(wave_context* ctx, const wave_geometry* geom, const float* m, 
   } else {
     CK(cudaMemsetAsync(ctx->d_phi, 0, sizeof(double), s));
   }
-  // adjoint sweep with the imaging condition
+  // adjoint sweep with the imaging condition: the stored tail first ...
   CK(cudaMemsetAsync(slot_ptr(W, P, 2), 0, 2 * P.slot_elems * 4, s));
-  if (!ckpt) {
-    TRY(adjoint_grad_steps(ctx, P, W, nt - 1, 1, r, Rr, &SS, 1, s));
-  } else {
-    for (int seg = nseg - 1; seg >= 0; --seg) {
-      const int L0 = seg * S;
-      const int L1 = std::min(L0 + S, nt);
-      float* c0 = ck + static_cast<long long>(seg) * 2 * P.slot_elems;
-      CK(cudaMemcpyAsync(slot_ptr(W, P, fslot(L0 - 1)), c0, P.slot_elems * 4, cudaMemcpyDeviceToDevice, s));
-      CK(cudaMemcpyAsync(slot_ptr(W, P, fslot(L0)), c0 + P.slot_elems, P.slot_elems * 4, cudaMemcpyDeviceToDevice, s));
-      // recompute u^{L0} .. u^{L1-1}, storing level n at index n - L0
-      TRY(forward_steps(ctx, P, W, L0, L1 - 1, qd, Sp, nullptr, nullptr, &SS, L0, L0, s));
-      TRY(store_level(ctx, P, W, fslot(L1 - 1), &SS, L1 - 1 - L0, s));
-      const int jlo = std::max(L0, 1);
-      if (L1 - 1 >= jlo) TRY(adjoint_grad_steps(ctx, P, W, L1 - 1, jlo, r, Rr, &SS, L0, s));
-    }
+  TRY(adjoint_grad_steps(ctx, P, W, nt - 1, std::max(T0, 1), r, Rr, &SS, T0, s));
+  // ... then the recomputed segments, last to first
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int L0 = seg * S;
+    const int L1 = std::min(L0 + S, T0);
+    float* c0 = ck + static_cast<long long>(seg) * 2 * P.slot_elems;
+    CK(cudaMemcpyAsync(slot_ptr(W, P, fslot(L0 - 1)), c0, P.slot_elems * 4, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(slot_ptr(W, P, fslot(L0)), c0 + P.slot_elems, P.slot_elems * 4, cudaMemcpyDeviceToDevice, s));
+    TRY(forward_steps(ctx, P, W, L0, L1 - 1, qd, Sp, nullptr, nullptr, &SS, L0, L0, s));
+    TRY(store_level(ctx, P, W, fslot(L1 - 1), &SS, L1 - 1 - L0, s));
+    const int jlo = std::max(L0, 1);
+    if (L1 - 1 >= jlo) TRY(adjoint_grad_steps(ctx, P, W, L1 - 1, jlo, r, Rr, &SS, L0, s));
   }
   TRY(launch(ctx, WAVE_KERNEL_OTHER, s,
              [&] { return launch_fold(P.g, W.grad, static_cast<float*>(gout.dev), s); }));

@@ -49,6 +49,10 @@ constexpr int kSlabY = 2;
 // A CTA owns BX x BY output columns (x, axis 1) and streams a chunk of planes
 // along axis 2 (3D); in 2D it owns one BX x BY tile of the single plane.
 // ---------------------------------------------------------------------------
+#ifndef WAVE_LEAD_MIN_R
+#define WAVE_LEAD_MIN_R 7
+#endif
+
 template <int R, int NDIM>
 struct StepTraits {
   static constexpr int BX = 64;                   // x outputs per CTA (16 threads x 4)
@@ -56,13 +60,22 @@ struct StepTraits {
   static constexpr int HX = (R <= 4) ? 4 : 8;     // x halo, rounded to 16 bytes for TMA
   static constexpr int RZ = (NDIM == 3) ? R : 0;  // halo along the streamed axis
   static constexpr int PF = (NDIM == 3) ? 2 : 0;  // extra planes prefetched ahead
-  static constexpr int NSU = RZ + 1 + PF;         // ring of u^n planes (with halo)
-  static constexpr int NSP = (NDIM == 3) ? 3 : 1; // ring of per-point tiles
-  static constexpr int UW = BX + 2 * HX;          // smem row length (floats)
-  static constexpr int UH = BY + 2 * R;           // smem rows
+  // Lead-plane design for radius 7-8: the register queue is fed from a
+  // small ring of interior boxes of plane z+R, and the halo box of the centre
+  // plane is loaded again (from L2) with the per-point tiles, so the shared
+  // ring holds only the prefetch depth instead of R+1+PF halo planes.
+  static constexpr bool LEAD = (NDIM == 3) && (R >= WAVE_LEAD_MIN_R);
+  static constexpr int UW = BX + 2 * HX;          // smem row length of a halo box (floats)
+  static constexpr int UH = BY + 2 * R;           // rows of a halo box
   static constexpr int U_BYTES = UW * UH * 4;                // bytes of one halo box
-  static constexpr int U_STRIDE = (U_BYTES + 127) / 128 * 128;  // stage spacing (128-byte aligned)
+  static constexpr int U_STRIDE = (U_BYTES + 127) / 128 * 128;  // halo box spacing (128-byte aligned)
   static constexpr int T_ELEMS = BX * BY;
+  // queue-feed ring: halo planes (classic) or interior boxes (lead)
+  static constexpr int NSU = LEAD ? PF + 1 : RZ + 1 + PF;
+  static constexpr int Q_BYTES = LEAD ? T_ELEMS * 4 : U_BYTES;
+  static constexpr int Q_STRIDE = LEAD ? T_ELEMS * 4 : U_STRIDE;
+  // per-plane ring: per-point tiles (+ the centre halo box in the lead design)
+  static constexpr int NSP = (NDIM == 3) ? 3 : 1;
   static constexpr int NCW = 8;                   // consumer warps
   static constexpr int NTHREADS = (NCW + 1) * 32; // + one producer warp
 };
@@ -72,17 +85,20 @@ template <int R, int NDIM, int MODE>
 struct StepLayout {
   using T = StepTraits<R, NDIM>;
   static constexpr int SNAP_ELEM = mode_snap_fmt(MODE) == 0 ? 4 : 2;
-  static constexpr int PREV_OFF = 0;
-  static constexpr int CM_OFF = T::T_ELEMS * 4;
-  static constexpr int G_OFF = 2 * T::T_ELEMS * 4;
-  static constexpr int S_OFF = 3 * T::T_ELEMS * 4;
-  static constexpr int P_BYTES = mode_is_grad(MODE) ? (3 * T::T_ELEMS * 4 + T::T_ELEMS * SNAP_ELEM)
-                                                    : 2 * T::T_ELEMS * 4;
+  static constexpr int HALO_OFF = 0;                        // lead design: centre halo box
+  static constexpr int PREV_OFF = T::LEAD ? T::U_STRIDE : 0;
+  static constexpr int CM_OFF = PREV_OFF + T::T_ELEMS * 4;
+  static constexpr int G_OFF = CM_OFF + T::T_ELEMS * 4;
+  static constexpr int S_OFF = G_OFF + T::T_ELEMS * 4;
+  static constexpr int TILE_BYTES = mode_is_grad(MODE) ? (3 * T::T_ELEMS * 4 + T::T_ELEMS * SNAP_ELEM)
+                                                       : 2 * T::T_ELEMS * 4;
+  static constexpr int P_TX = (T::LEAD ? T::U_BYTES : 0) + TILE_BYTES;  // bytes landing per plane stage
+  static constexpr int P_BYTES = PREV_OFF + TILE_BYTES;                   // stage spacing
   static_assert(P_BYTES % 128 == 0, "per-point stage must keep 128-byte alignment");
   // 2*(NSU+NSP) mbarriers + an abort flag, padded to 128 bytes
   static constexpr int BAR_BYTES = ((16 * (T::NSU + T::NSP) + 16 + 127) / 128) * 128;
   static constexpr int U_OFF = BAR_BYTES;
-  static constexpr int PST_OFF = U_OFF + T::NSU * T::U_STRIDE;
+  static constexpr int PST_OFF = U_OFF + T::NSU * T::Q_STRIDE;
   static constexpr int SMEM = PST_OFF + T::NSP * P_BYTES + 128;  // + runtime 128-byte alignment
 };
 
