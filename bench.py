@@ -57,6 +57,10 @@ def parse_args():
     ap.add_argument("--requests", type=int, default=400, help="serve mode: number of requests")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serve mode: HBM budget for resident requests")
     ap.add_argument("--max-resident", type=int, default=32, help="serve mode: stream slots")
+    ap.add_argument("--workload", default="throughput", choices=["throughput", "paper_demo", "large"],
+                    help="throughput: 512^3 two-layer + perturbation (default); paper_demo: the paper's 3D "
+                         "demonstration shape 201x201x70 + 40 (h = 15 m, order 14, 1 s, 10 Hz); large: "
+                         "1000x1000x600 + 40, order 16, layered model with a salt body")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-nz", type=int, default=8, help="physical depth points of the CPU sample")
@@ -67,8 +71,28 @@ def parse_args():
 # workload
 # ---------------------------------------------------------------------------
 
-def make_workload(n, nbl, so, nt):
+def make_workload(n, nbl, so, nt, kind="throughput"):
     from paper_1608_08658_gb300 import inputs
+    if kind == "paper_demo":
+        # Sec. V-D demonstration: 201 x 201 x 70 + 40-point layer, h = 15 m, Ricker 10 Hz, 1 s, order 14;
+        # the paper's velocity model is not given: a seeded layered model stands in for it
+        shape, h = (201, 201, 70), (15.0, 15.0, 15.0)
+        prof = inputs.layered_profile(shape[2], h[2], 5, v_min=1.5, v_max=3.5, seed=21)
+        v0 = np.broadcast_to(prof[:, None, None], shape[::-1]).copy()
+        ext = (shape[0] - 1) * h[0]
+        src = np.array([[0.5 * ext, 0.5 * ext, 30.0]], dtype=np.float32)
+        rec = inputs.surface_grid_receivers(shape[0], shape[1], h[:2], 30.0)
+        return dict(shape=shape, spacing=h, nbl=40, so=14, nt=nt, v0=v0, v_true=v0, src=src, rec=rec,
+                    vmax=float(v0.max()), f0=0.010, duration_ms=1000.0, kind=kind)
+    if kind == "large":
+        shape, h = (1000, 1000, 600), (10.0, 10.0, 10.0)
+        v0 = inputs.layered_salt_velocity(shape, h)
+        src = np.array([[4995.0, 4995.0, 20.0]], dtype=np.float32)
+        g = np.linspace(0.0, 9990.0, 100)
+        X, Y = np.meshgrid(g, g, indexing="xy")
+        rec = np.stack([X.ravel(), Y.ravel(), np.full(X.size, 20.0)], axis=1).astype(np.float32)
+        return dict(shape=shape, spacing=h, nbl=40, so=16, nt=3000, v0=v0, v_true=v0, src=src, rec=rec,
+                    vmax=4.5, f0=0.010, kind=kind)
     shape = (n, n, n)
     h = (10.0, 10.0, 10.0)
     v0 = inputs.two_layer_random_velocity(shape, h, 1.5, 2.5, sigma=0.0)
@@ -77,13 +101,22 @@ def make_workload(n, nbl, so, nt):
     src = np.array([[0.5 * ext, 0.5 * ext, 20.0]], dtype=np.float32)
     rec = inputs.surface_grid_receivers(n, n, (h[0], h[1]), 20.0)
     return dict(shape=shape, spacing=h, nbl=nbl, so=so, nt=nt, v0=v0, v_true=v_true, src=src, rec=rec,
-                vmax=float(v_true.max()), f0=0.015)
+                vmax=float(v_true.max()), f0=0.015, kind=kind)
 
 
 def workload_config(w, snap, mode="gradient"):
     n = w["shape"][0]
     ncomp = n + 2 * w["nbl"]
     what = "FWI gradient" if mode == "gradient" else "forward modelling"
+    if w.get("kind", "throughput") != "throughput":
+        comp = [s + 2 * w["nbl"] for s in w["shape"]]
+        name = {"paper_demo": "paper 3D demonstration shape (Sec. V-D), synthetic layered model",
+                "large": "large layered model with salt body"}[w["kind"]]
+        return {"workload": "3D %s %s: %s + %d sponge = %s points, h=%g m, so=%d, nt=%d" % (
+                    what, name, "x".join(map(str, w["shape"])), w["nbl"], "x".join(map(str, comp)), w["spacing"][0],
+                    w["so"], w["nt"]),
+                "grid": list(w["shape"]), "nbl": w["nbl"], "space_order": w["so"], "nt": w["nt"], "snap_mode": snap,
+                "l2": "inputs larger than L2" if np.prod(comp) * 4 > 129e6 else "fields smaller than L2"}
     return {
         "workload": "3D " + what + " %d^3 (+%d sponge = %d^3), h=10 m, so=%d, nt=%d, two-layer 1.5/2.5 km/s + 5%% "
                     "perturbation, 1 Ricker 15 Hz, %dx%d surface receivers" % (n, w["nbl"], ncomp, w["so"], w["nt"],
@@ -257,10 +290,13 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
-    w = make_workload(args.n, args.nbl, args.so, args.nt)
-    so, nt = args.so, args.nt
+    w = make_workload(args.n, args.nbl, args.so, args.nt, args.workload)
+    so = w["so"]
     geom = wave.Geometry(shape=w["shape"], spacing=w["spacing"], nbl=w["nbl"], sponge_vref=w["vmax"])
     dt = 0.4 * wave.wave_dt_max(w["spacing"], so, w["vmax"])
+    if "duration_ms" in w:
+        w["nt"] = int(np.ceil(w["duration_ms"] / dt)) + 1
+    nt = w["nt"]
     q = wave.wave_ricker(nt, dt, w["f0"]).reshape(nt, 1)
     m0 = (1.0 / w["v0"] ** 2).astype(np.float32)
     mt = (1.0 / w["v_true"] ** 2).astype(np.float32)
@@ -328,7 +364,7 @@ def run_ours(args, rank, world, local_rank):
     dom = max(kernels, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["launches"])
     ach = kernels[dom]["achieved_gbs"]
     roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": measured_traffic(dom, npts) if args.so == 8 and not fmt16 else None, "kernel": dom, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs copy test)"
+                "traffic": measured_traffic(dom, npts) if so == 8 and not fmt16 else None, "kernel": dom, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs copy test)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s", "bytes_per_point": bpp[dom],
                 "points_per_launch": npts}
 

@@ -141,6 +141,11 @@ WAVE_API int wave_context_trim(wave_context* ctx);
  * budget (default). */
 WAVE_API int wave_context_set_checkpoint_interval(wave_context* ctx, int steps);
 
+/* Storage plan of the context's last wave_gradient / wave_jacobian_adjoint
+ * call: snapshot buffer levels F, parts per checkpointed segment k, and the
+ * number of checkpointed segments (0 = full storage). */
+WAVE_API int wave_context_storage_plan(const wave_context* ctx, int* levels, int* parts, int* segments);
+
 /* Text of a status code, and the last error message of a context. */
 WAVE_API const char* wave_error_string(int status);
 WAVE_API const char* wave_last_error(const wave_context* ctx);

@@ -72,6 +72,7 @@ struct wave_context {
   int64_t launches[WAVE_KERNEL_KINDS] = {};
   double ms[WAVE_KERNEL_KINDS] = {};
   int ckpt_interval = 0;
+  int last_plan[4] = {0, 0, 0, 0};  // fmt, buffer levels, parts per segment, segments
 };
 
 namespace {
@@ -974,16 +975,20 @@ int adjoint_impl(wave_context* ctx, const wave_geometry* geom, const float* m, c
 // ---------------------------------------------------------------- gradient
 // Storage plan for the forward wavefield of Eq. 3.  A buffer of F snapshot
 // levels first holds the last F levels (nt-F .. nt-1), stored during the
-// forward sweep; the earlier levels are recomputed from exact FP32
-// checkpoints in segments of S <= F levels, reusing the same buffer once the
-// adjoint sweep has consumed the stored tail.  F = nt-1 is full storage (no
-// checkpoints); F = S is pure checkpointing.
+// forward sweep; the earlier levels [0, T0) are covered by segments of
+// S = k*F levels that start at exact FP32 checkpoints (u^{k-1}, u^k).  In
+// the reverse sweep each segment is rebuilt part by part, last part first:
+// the part [A, A+F) is recomputed from the segment checkpoint into the same
+// buffer, then swept by the adjoint.  k = 1 is classic two-level
+// checkpointing, F = nt-1 is full storage; larger k trades recomputation
+// ((k+1)/2 passes over the early part) for fewer checkpoints.
 struct StoragePlan {
   int fmt = 0;   // 0 FP32, 1 BF16, 2 FP16
   int F = 0;     // levels in the snapshot buffer
-  int S = 0;     // segment length of the recomputed part
+  int k = 1;     // buffer-lengths per checkpointed segment
+  int S = 0;     // segment length k*F
   int T0 = 1;    // first stored level of the tail
-  int nseg = 0;  // recomputed segments covering levels [0, T0)
+  int nseg = 0;  // checkpointed segments covering levels [0, T0)
 };
 
 int plan_storage(wave_context* ctx, Prob& P, int mode, StoragePlan* plan) {
@@ -1019,27 +1024,35 @@ int plan_storage(wave_context* ctx, Prob& P, int mode, StoragePlan* plan) {
     case WAVE_SNAP_AUTO: f = 0; ckpt = level_bytes(0) * static_cast<size_t>(nt - 1) > avail; break;
   }
   const size_t lb = level_bytes(f);
-  int F = nt - 1;
+  int F = nt - 1, k = 1;
   if (ckpt) {
     if (ctx->ckpt_interval > 0) {
       F = std::min(ctx->ckpt_interval, nt - 1);
     } else {
-      // largest buffer such that the buffer plus the checkpoints fit
-      F = static_cast<int>(std::min<size_t>(avail / lb, static_cast<size_t>(nt - 1)));
-      while (F > 1) {
-        const int T0 = nt - F;
-        const size_t nseg = static_cast<size_t>((T0 + F - 1) / F);
-        if (static_cast<size_t>(F) * lb + nseg * 2 * fb <= avail) break;
-        --F;
-      }
-      F = std::max(F, 1);
+      // smallest k for which some buffer size fits; the largest such buffer
+      auto fits = [&](int FF, int kk) {
+        const int T0 = nt - FF;
+        const size_t nseg = static_cast<size_t>((T0 + kk * FF - 1) / (kk * FF));
+        return static_cast<size_t>(FF) * lb + nseg * 2 * fb <= avail;
+      };
+      const int Fcap = static_cast<int>(std::min<size_t>(avail / lb, static_cast<size_t>(nt - 1)));
+      F = 0;
+      for (k = 1; k <= 64 && F == 0; k *= 2)
+        for (int FF = Fcap; FF >= 1; --FF)
+          if (fits(FF, k)) {
+            F = FF;
+            break;
+          }
+      k = F ? k / 2 : 1;
+      if (F == 0) return fail(ctx, WAVE_ERR_OUT_OF_MEMORY, "the forward wavefield storage does not fit in memory");
     }
   }
   plan->fmt = f;
   plan->F = F;
-  plan->S = F;
+  plan->k = k;
+  plan->S = k * F;
   plan->T0 = nt - F;
-  plan->nseg = plan->T0 > 1 ? (plan->T0 + F - 1) / F : 0;
+  plan->nseg = plan->T0 > 1 ? (plan->T0 + plan->S - 1) / plan->S : 0;
   return WAVE_OK;
 }
 
@@ -1054,8 +1067,6 @@ int gradient_impl(wave_context* ctx, const wave_geometry* geom, const float* m, 
   const long long ns = src ? src->n : 0, nr = rec ? rec->n : 0;
   if (ns > 0 && !q) return fail(ctx, WAVE_ERR_INVALID_ARG, "source traces are NULL");
   if (nr > 0 && !d_obs && !y_given) return fail(ctx, WAVE_ERR_INVALID_ARG, "observed data are NULL");
-  StoragePlan plan;
-  TRY(plan_storage(ctx, P, snap_mode, &plan));
   const void* mdev;
   TRY(stage_in(ctx, "m", m, P.phys_elems * 4, s, &mdev));
   const void* qdev = nullptr;
@@ -1086,6 +1097,13 @@ int gradient_impl(wave_context* ctx, const wave_geometry* geom, const float* m, 
   }
   const float* qd = static_cast<const float*>(qdev);
   // storage: a buffer of plan.F levels; checkpoints at the segment starts
+  // (planned after every other buffer of the call is held)
+  StoragePlan plan;
+  TRY(plan_storage(ctx, P, snap_mode, &plan));
+  ctx->last_plan[0] = plan.fmt;
+  ctx->last_plan[1] = plan.F;
+  ctx->last_plan[2] = plan.k;
+  ctx->last_plan[3] = plan.nseg;
   SnapStore SS;
   const int T0 = plan.T0, S = plan.S, nseg = plan.nseg;
   float* ck = nullptr;
@@ -1129,17 +1147,22 @@ int gradient_impl(wave_context* ctx, const wave_geometry* geom, const float* m, 
   // adjoint sweep with the imaging condition: the stored tail first ...
   CK(cudaMemsetAsync(slot_ptr(W, P, 2), 0, 2 * P.slot_elems * 4, s));
   TRY(adjoint_grad_steps(ctx, P, W, nt - 1, std::max(T0, 1), r, Rr, &SS, T0, s));
-  // ... then the recomputed segments, last to first
+  // ... then the recomputed segments, last to first, each part by part
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int L0 = seg * S;
     const int L1 = std::min(L0 + S, T0);
-    float* c0 = ck + static_cast<long long>(seg) * 2 * P.slot_elems;
-    CK(cudaMemcpyAsync(slot_ptr(W, P, fslot(L0 - 1)), c0, P.slot_elems * 4, cudaMemcpyDeviceToDevice, s));
-    CK(cudaMemcpyAsync(slot_ptr(W, P, fslot(L0)), c0 + P.slot_elems, P.slot_elems * 4, cudaMemcpyDeviceToDevice, s));
-    TRY(forward_steps(ctx, P, W, L0, L1 - 1, qd, Sp, nullptr, nullptr, &SS, L0, L0, s));
-    TRY(store_level(ctx, P, W, fslot(L1 - 1), &SS, L1 - 1 - L0, s));
-    const int jlo = std::max(L0, 1);
-    if (L1 - 1 >= jlo) TRY(adjoint_grad_steps(ctx, P, W, L1 - 1, jlo, r, Rr, &SS, L0, s));
+    const float* c0 = ck + static_cast<long long>(seg) * 2 * P.slot_elems;
+    for (int A = L0 + ((L1 - L0 - 1) / plan.F) * plan.F; A >= L0; A -= plan.F) {
+      const int B = std::min(A + plan.F, L1);
+      CK(cudaMemcpyAsync(slot_ptr(W, P, fslot(L0 - 1)), c0, P.slot_elems * 4, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(slot_ptr(W, P, fslot(L0)), c0 + P.slot_elems, P.slot_elems * 4, cudaMemcpyDeviceToDevice,
+                         s));
+      if (A > L0) TRY(forward_steps(ctx, P, W, L0, A, qd, Sp, nullptr, nullptr, nullptr, 0, 0, s));
+      TRY(forward_steps(ctx, P, W, A, B - 1, qd, Sp, nullptr, nullptr, &SS, A, A, s));
+      TRY(store_level(ctx, P, W, fslot(B - 1), &SS, B - 1 - A, s));
+      const int jlo = std::max(A, 1);
+      if (B - 1 >= jlo) TRY(adjoint_grad_steps(ctx, P, W, B - 1, jlo, r, Rr, &SS, A, s));
+    }
   }
   TRY(launch(ctx, WAVE_KERNEL_OTHER, s,
              [&] { return launch_fold(P.g, W.grad, static_cast<float*>(gout.dev), s); }));
@@ -1652,6 +1675,14 @@ int wave_session_destroy(wave_session* S) {
   sess_free(S);
   cudaGetLastError();
   delete S;
+  return WAVE_OK;
+}
+
+int wave_context_storage_plan(const wave_context* ctx, int* levels, int* parts, int* segments) {
+  if (!ctx) return WAVE_ERR_INVALID_ARG;
+  if (levels) *levels = ctx->last_plan[1];
+  if (parts) *parts = ctx->last_plan[2];
+  if (segments) *segments = ctx->last_plan[3];
   return WAVE_OK;
 }
 

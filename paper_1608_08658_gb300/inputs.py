@@ -204,3 +204,30 @@ def request_points(req):
         X, Y = np.meshgrid(g, g, indexing="xy")
         rec = np.stack([X.ravel(), Y.ravel(), np.full(X.size, 20.0)], axis=1).astype(np.float32)
     return src, rec
+
+
+def gradient_models(shape_xyz, spacing, seed=11):
+    """FWI gradient workload: background v(z) = 1.5 + 0.6 z[km] and the true
+    model with three seeded Gaussian anomalies (+-0.2 km/s, sigma 150 m)."""
+    v0 = linear_gradient_velocity(shape_xyz, spacing)
+    return v0, v0 + gaussian_anomalies(shape_xyz, spacing, n=3, amp=0.2, sigma_m=150.0, seed=seed)
+
+
+def layered_salt_velocity(shape_xyz, spacing, n_layers=8, v_min=1.5, v_max=4.5, v_salt=4.5,
+                          semi_axes_m=(1500.0, 1000.0, 600.0), seed=5):
+    """Large-model workload: ``n_layers`` flat layers (1D profile, see
+    ``layered_profile``) with an ellipsoidal salt-like body of velocity v_salt
+    centred mid-model (jittered by the seed), built plane by plane in float32."""
+    nx, ny, nz = shape_xyz
+    prof = layered_profile(nz, spacing[2], n_layers, v_min, v_max, seed=seed).astype(np.float32)
+    r = rng(seed + 1)
+    ext = [(s - 1) * h for s, h in zip(shape_xyz, spacing)]
+    c = [0.5 * e + r.uniform(-0.05, 0.05) * e for e in ext]
+    x = ((np.arange(nx) * spacing[0] - c[0]) / semi_axes_m[0]) ** 2
+    y = ((np.arange(ny) * spacing[1] - c[1]) / semi_axes_m[1]) ** 2
+    xy = (y[:, None] + x[None, :]).astype(np.float32)
+    v = np.empty((nz, ny, nx), dtype=np.float32)
+    for k in range(nz):
+        zz = ((k * spacing[2] - c[2]) / semi_axes_m[2]) ** 2
+        v[k] = np.where(xy + zz <= 1.0, np.float32(v_salt), prof[k])
+    return v

@@ -93,6 +93,8 @@ _SIGS = {
     "wave_session_read": (ctypes.c_int, [_P, _P]),
     "wave_session_destroy": (ctypes.c_int, [_P]),
     "wave_context_budget_free": (ctypes.c_size_t, [_P]),
+    "wave_context_storage_plan": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                                 ctypes.POINTER(ctypes.c_int)]),
 }
 
 _lib = None
@@ -279,6 +281,12 @@ class Context:
 
     def budget_free(self):
         return int(lib().wave_context_budget_free(self.handle))
+
+    def storage_plan(self):
+        """(buffer levels, parts per segment, segments) of the last gradient call."""
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self, lib().wave_context_storage_plan(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
 
 
 class Session:
