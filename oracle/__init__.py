@@ -11,7 +11,9 @@ restatement of the method in float64, written from the paper:
   * ``model``   -- padding, sponge profile, CFL limit, Ricker wavelet (Sec. V-C/D),
   * ``interp``  -- sparse-point (bi/tri-linear) interpolation operators (Sec. IV),
   * ``wave``    -- Laplacian, forward leapfrog (Listing 1, Eq. 1), adjoint
-                   (Listing 2, Eq. 4), objective (Eq. 2), gradient (Eq. 3).
+                   (Listing 2, Eq. 4), objective (Eq. 2), gradient (Eq. 3),
+                   and the linearised (Born) operator J whose transpose Eq. 3
+                   applies.
 
 Where the paper is silent or garbled the oracle takes one explicit reading; the
 list of readings is kept with the design notes of the repository.  Every

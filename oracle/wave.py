@@ -204,3 +204,41 @@ def identity_operator(shape):
     """Full-field restriction (every cell a point), for operator-level tests."""
     n = int(np.prod(shape))
     return sp.identity(n, format="csr", dtype=np.float64)
+
+
+def born_op(m, eta, spacing, dt, nt, space_order, q, dm, Ps, Pr):
+    """Linearised (Born) modelling J dm on the computational grid.
+
+    Differentiating the rows ``a u^{k+1} - b u^k + c u^{k-1} = P_s^T q^k`` with
+    respect to m in the direction dm (a, b, c depend on m through m/dt^2,
+    2m/dt^2, m/dt^2) gives the scattered field
+        a du^{k+1} - b du^k + c du^{k-1} = -dm (u^{k+1} - 2u^k + u^{k-1}) / dt^2
+    with zero initial state, and the linearised data dd^n = P_r du^n.  The
+    background u is the forward field of ``forward_op``.
+    """
+    m = np.asarray(m, dtype=np.float64)
+    eta = np.asarray(eta, dtype=np.float64)
+    dm = np.asarray(dm, dtype=np.float64)
+    fwd = forward_op(m, eta, spacing, dt, nt, space_order, q, Ps, Pr, save=True)
+    u = fwd.history
+    shape = m.shape
+    a, c = _coefficients(m, eta, dt)
+    du_prev = np.zeros(shape)
+    du_cur = np.zeros(shape)
+    dd = np.zeros((nt, Pr.shape[0]))
+    for k in range(nt - 1):
+        u_prev = u[k - 1] if k >= 1 else np.zeros(shape)
+        src = -dm * (u[k + 1] - 2.0 * u[k] + u_prev) / dt ** 2
+        b_du = 2.0 * m / dt ** 2 * du_cur + laplacian(du_cur, space_order, spacing)
+        du_next = (b_du - c * du_prev + src) / a
+        dd[k + 1] = Pr @ du_next.ravel()
+        du_prev, du_cur = du_cur, du_next
+    return dd
+
+
+def born(geom, m_phys, dm_phys, dt, nt, space_order, q, src_coords, rec_coords):
+    """J dm for a physical model perturbation (padded like the model)."""
+    m = pad_model(geom, m_phys)
+    dm = pad_model(geom, dm_phys)
+    Ps, Pr = operators(geom, src_coords, rec_coords)
+    return born_op(m, damping(geom), geom.spacing, dt, nt, space_order, q, dm, Ps, Pr)

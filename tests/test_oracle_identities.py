@@ -207,3 +207,26 @@ def test_windowed_model_and_damping_equal_crops(ndim):
     sl = tuple(slice(a, b) for a, b in win)
     np.testing.assert_array_equal(model.pad_model(geom, m, window=win), full_m[sl])
     np.testing.assert_array_equal(model.damping(geom, window=win), full_e[sl])
+
+
+@pytest.mark.parametrize("ndim,so", [(2, 4), (3, 8)])
+def test_born_is_the_derivative_of_the_forward_map(ndim, so):
+    """J dm against central differences of F (error O(eps^2)) and against the
+    gradient through <J dm, y> = <dm, J^T y> (J^T y: gradient with residual y)."""
+    nt = 50
+    geom, m, src, rec, dt = _case(ndim, so, seed=12, nsrc=1, nrec=8)
+    rng = np.random.default_rng(13)
+    q = rng.standard_normal((nt, 1))
+    dm = 0.1 * m * rng.uniform(-1, 1, size=m.shape)
+    jd = wave.born(geom, m, dm, dt, nt, so, q, src, rec)
+    errs = []
+    for eps in (1e-2, 5e-3):
+        fp = wave.forward(geom, m + eps * dm, dt, nt, so, q, src, rec).d
+        fm = wave.forward(geom, m - eps * dm, dt, nt, so, q, src, rec).d
+        errs.append(np.linalg.norm((fp - fm) / (2 * eps) - jd) / np.linalg.norm(jd))
+    assert errs[0] < 1e-3 and errs[1] < errs[0] / 3.5, errs
+    y = rng.standard_normal((nt, len(rec)))
+    d_pred = wave.forward(geom, m, dt, nt, so, q, src, rec).d
+    jty, _ = wave.gradient(geom, m, dt, nt, so, q, src, rec, d_pred - y)
+    lhs, rhs = np.sum(jd * y), np.sum(dm * jty)
+    assert abs(lhs - rhs) <= 1e-11 * max(abs(lhs), abs(rhs)), (lhs, rhs)
