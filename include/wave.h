@@ -256,6 +256,17 @@ WAVE_API int wave_session_destroy(wave_session* session);
 /* Budget left for new sessions and workspace (0 when the context has no cap). */
 WAVE_API size_t wave_context_budget_free(const wave_context* ctx);
 
+/* Linearised (Born) modelling: dd = J dm, the derivative of wave_forward's
+ * receiver data with respect to m in the direction dm (J is the Jacobian whose
+ * transpose Eq. 3 applies; wave_jacobian_adjoint computes J^T y).  The
+ * scattered field solves the rows of Eq. 1 differentiated in m:
+ *   a du^{k+1} - b du^k + c du^{k-1} = -dm (u^{k+1} - 2u^k + u^{k-1}) / dt^2,
+ * du^{-1} = du^0 = 0, dd^n = P_r du^n; dm is padded like m.
+ * dm: physical grid like m; d_out: [nt][n_r].  Errors: as wave_forward. */
+WAVE_API int wave_born(wave_context* ctx, const wave_geometry* geom, const float* m, const float* dm,
+                       const wave_points* src, const float* q, const wave_points* rec, float* d_out, float dt,
+                       int nt, int space_order, void* stream);
+
 /* ---- helpers (host-side, no device work) ---------------------------------- */
 
 /* Centred second-derivative weights [w_0, w_1, .., w_R], R = space_order/2

@@ -41,6 +41,27 @@ __global__ void setup_cm_kernel(GridDims g, const float* __restrict__ m, float* 
   }
 }
 
+// A physical field extended onto the computational grid by edge replication
+// (the padding of the model, applied to a model perturbation).
+__global__ void pad_field_kernel(GridDims g, const float* __restrict__ phys, float* __restrict__ comp) {
+  const long long total = static_cast<long long>(g.NZ) * g.NY * g.pitch;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(i % g.pitch);
+    const long long r = i / g.pitch;
+    const int y = static_cast<int>(r % g.NY);
+    const int z = static_cast<int>(r / g.NY);
+    float v = 0.f;
+    if (x < g.NX) {
+      const int px = min(max(x - g.nblx, 0), g.PX - 1);
+      const int py = min(max(y - g.nbly, 0), g.PY - 1);
+      const int pz = min(max(z - g.nblz, 0), g.PZ - 1);
+      v = phys[(static_cast<long long>(pz) * g.PY + py) * g.PX + px];
+    }
+    comp[i] = v;
+  }
+}
+
 // min and max of a positive float array via the ordering of IEEE bit patterns.
 __global__ void minmax_kernel(const float* __restrict__ m, long long n, unsigned int* out) {
   unsigned int lo = 0xffffffffu, hi = 0u;
@@ -320,6 +341,12 @@ __global__ void fill_zero_kernel(float* p, long long n) {
 cudaError_t launch_setup_cm(const GridDims& g, const float* m_phys, float* cm, float dt2, cudaStream_t s) {
   const long long n = static_cast<long long>(g.NZ) * g.NY * g.pitch;
   setup_cm_kernel<<<blocks_for(n), kThreads, 0, s>>>(g, m_phys, cm, dt2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pad_field(const GridDims& g, const float* phys, float* comp, cudaStream_t s) {
+  const long long n = static_cast<long long>(g.NZ) * g.NY * g.pitch;
+  pad_field_kernel<<<blocks_for(n), kThreads, 0, s>>>(g, phys, comp);
   return cudaGetLastError();
 }
 

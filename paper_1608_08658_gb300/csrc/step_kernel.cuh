@@ -150,10 +150,8 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
       prefetch_tensormap(&tm_u);
       prefetch_tensormap(&tm_p);
       prefetch_tensormap(&tm_cm);
-      if (mode_is_grad(MODE)) {
-        prefetch_tensormap(&tm_g);
-        prefetch_tensormap(&tm_s);
-      }
+      if (mode_loads_g(MODE)) prefetch_tensormap(&tm_g);
+      if (mode_is_grad(MODE)) prefetch_tensormap(&tm_s);
       int issuedU = 0, issuedP = 0;
       bool ok = true;
       for (int s = 0; s < nU; ++s) {
@@ -177,10 +175,8 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
             tma_load_4d(pd + L::HALO_OFF, &tm_u, x0 - T::HX, y0 - R, z0 + j, p.cur, &fullP[ps]);
           tma_load_4d(pd + L::PREV_OFF, &tm_p, x0, y0, z0 + j, p.prev, &fullP[ps]);
           tma_load_3d(pd + L::CM_OFF, &tm_cm, x0, y0, z0 + j, &fullP[ps]);
-          if (mode_is_grad(MODE)) {
-            tma_load_3d(pd + L::G_OFF, &tm_g, x0, y0, z0 + j, &fullP[ps]);
-            tma_load_4d(pd + L::S_OFF, &tm_s, x0, y0, z0 + j, p.snap_level, &fullP[ps]);
-          }
+          if (mode_loads_g(MODE)) tma_load_3d(pd + L::G_OFF, &tm_g, x0, y0, z0 + j, &fullP[ps]);
+          if (mode_is_grad(MODE)) tma_load_4d(pd + L::S_OFF, &tm_s, x0, y0, z0 + j, p.snap_level, &fullP[ps]);
           issuedP = j + 1;
         }
       }
@@ -354,8 +350,6 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
         }
       }
     }
-    const float4 lap = make_float4(la.x, la.y, lb.x, lb.y);
-
     if constexpr (!T::LEAD) {
       good = mbar_wait_bounded(&fullP[ps], (j / T::NSP) & 1, abort_flag, kWaitLimitNs);
       if (!__all_sync(0xffffffffu, good)) return false;
@@ -363,7 +357,14 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
     const unsigned char* Pst = Pbase + ps * L::P_BYTES;
     const float4 prev = *reinterpret_cast<const float4*>(Pst + L::PREV_OFF + tofs);
     const float4 cm = *reinterpret_cast<const float4*>(Pst + L::CM_OFF + tofs);
+    if constexpr (MODE == MODE_SRC) {
+      // source field of the scattered wavefield enters like the Laplacian
+      const float4 src = *reinterpret_cast<const float4*>(Pst + L::G_OFF + tofs);
+      la = __fadd2_rn(la, make_float2(src.x, src.y));
+      lb = __fadd2_rn(lb, make_float2(src.z, src.w));
+    }
 
+    const float4 lap = make_float4(la.x, la.y, lb.x, lb.y);
     const int gz = z0 + j;
     const float ez = NDIM == 3 ? sponge_term(gz, p.NZ, p.nblz, p.emz) : 0.f;
     float4 out;
@@ -398,6 +399,16 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
         if (lane == 0 && gy < p.NY)
           p.scale_out[(static_cast<long long>(gz) * p.slabs_y + (gy >> 1)) * p.slabs_x + blockIdx.x] = s;
       }
+    }
+    if constexpr (MODE == MODE_BORN_SRC) {
+      // Born source of the scattered field: -dm (new - 2 cur + prev) / dt^2
+      const float4 dm = *reinterpret_cast<const float4*>(Pst + L::G_OFF + tofs);
+      float4 sb;
+      sb.x = -dm.x * (out.x - 2.f * c.x + prev.x) * p.inv_dt2;
+      sb.y = -dm.y * (out.y - 2.f * c.y + prev.y) * p.inv_dt2;
+      sb.z = -dm.z * (out.z - 2.f * c.z + prev.z) * p.inv_dt2;
+      sb.w = -dm.w * (out.w - 2.f * c.w + prev.w) * p.inv_dt2;
+      if (store_ok) *reinterpret_cast<float4*>(p.grad + idx) = sb;
     }
     if constexpr (mode_is_grad(MODE)) {
       float s = 1.f;
@@ -464,6 +475,8 @@ static cudaError_t launch_modes(int mode, const StepMaps& maps, const StepParams
     case MODE_GRAD_F32: return launch_one<R, NDIM, MODE_GRAD_F32>(maps, p, grid, s);
     case MODE_GRAD_BF16: return launch_one<R, NDIM, MODE_GRAD_BF16>(maps, p, grid, s);
     case MODE_GRAD_F16: return launch_one<R, NDIM, MODE_GRAD_F16>(maps, p, grid, s);
+    case MODE_BORN_SRC: return launch_one<R, NDIM, MODE_BORN_SRC>(maps, p, grid, s);
+    case MODE_SRC: return launch_one<R, NDIM, MODE_SRC>(maps, p, grid, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -478,6 +491,8 @@ static int smem_modes(int mode) {
     case MODE_GRAD_F32: return StepLayout<R, NDIM, MODE_GRAD_F32>::SMEM;
     case MODE_GRAD_BF16: return StepLayout<R, NDIM, MODE_GRAD_BF16>::SMEM;
     case MODE_GRAD_F16: return StepLayout<R, NDIM, MODE_GRAD_F16>::SMEM;
+    case MODE_BORN_SRC: return StepLayout<R, NDIM, MODE_BORN_SRC>::SMEM;
+    case MODE_SRC: return StepLayout<R, NDIM, MODE_SRC>::SMEM;
     default: return -1;
   }
 }

@@ -972,6 +972,81 @@ int adjoint_impl(wave_context* ctx, const wave_geometry* geom, const float* m, c
   return WAVE_OK;
 }
 
+// ---------------------------------------------------------------- Born modelling
+// J dm: the background field u (with the Born source S written by its step)
+// and the scattered field du (slots 2-3) advance together; S is corrected at
+// the injected source cells like the imaging condition of the gradient.
+int born_impl(wave_context* ctx, const wave_geometry* geom, const float* m, const float* dm, const wave_points* src,
+              const float* q, const wave_points* rec, float* d_out, float dt, int nt, int so, cudaStream_t s) {
+  TRY(check_common(ctx, geom, m));
+  if (!dm) return fail(ctx, WAVE_ERR_INVALID_ARG, "model perturbation is NULL");
+  Prob P;
+  TRY(prepare(ctx, geom, dt, nt, so, &P));
+  const long long ns = src ? src->n : 0, nr = rec ? rec->n : 0;
+  if (ns > 0 && !q) return fail(ctx, WAVE_ERR_INVALID_ARG, "source traces are NULL");
+  if (nr > 0 && !d_out) return fail(ctx, WAVE_ERR_INVALID_ARG, "receiver output is NULL");
+  const void *mdev, *dmdev;
+  TRY(stage_in(ctx, "m", m, P.phys_elems * 4, s, &mdev));
+  TRY(stage_in(ctx, "dm", dm, P.phys_elems * 4, s, &dmdev));
+  const void* qdev = nullptr;
+  if (ns > 0) TRY(stage_in(ctx, "q", q, static_cast<size_t>(nt) * ns * 4, s, &qdev));
+  Work W;
+  TRY(prepare_fields(ctx, P, static_cast<const float*>(mdev), s, true, &W));  // W.grad holds S
+  void* p = nullptr;
+  TRY(ws_get(ctx, "dm_comp", P.slot_elems * 4, &p));
+  float* dmc = static_cast<float*>(p);
+  TRY(launch(ctx, WAVE_KERNEL_OTHER, s,
+             [&] { return launch_pad_field(P.g, static_cast<const float*>(dmdev), dmc, s); }));
+  StepMaps maps_born = W.maps, maps_src = W.maps;  // third tile: dm for the background, S for du
+  {
+    const GridDims& g = P.g;
+    cuuint64_t dims[3] = {(cuuint64_t)g.NX, (cuuint64_t)g.NY, (cuuint64_t)g.NZ};
+    cuuint64_t str[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.pitch * g.NY * 4};
+    cuuint32_t box[3] = {(cuuint32_t)step_bx(), (cuuint32_t)step_by(P.R, P.ndim), 1};
+    TRY(make_map(ctx, &maps_born.g, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, dmc, dims, str, box));
+  }
+  wave_points empty{0, nullptr};
+  PointSetDev *Sp = nullptr, *Rr = nullptr;
+  TRY(prepare_points(ctx, P, src ? src : &empty, s, &Sp));
+  TRY(prepare_points(ctx, P, rec ? rec : &empty, s, &Rr));
+  OutStage dout;
+  TRY(stage_out(ctx, "d_born", d_out, static_cast<size_t>(nt) * nr * 4, &dout));
+  TRY(inject_coefficients(ctx, P, W, Sp, s));
+  CK(cudaMemsetAsync(W.fields, 0, 4 * P.slot_elems * 4, s));
+  CK(cudaMemsetAsync(W.grad, 0, P.slot_elems * 4, s));
+  float* d = static_cast<float*>(dout.dev);
+  if (nr > 0) CK(cudaMemsetAsync(d, 0, nr * 4, s));  // du^0 = 0
+  InjectSet isrc = inject_set(Sp);
+  GatherSet grec = gather_set(P, Rr);
+  const float* qd = static_cast<const float*>(qdev);
+  P.sp.grad = W.grad;
+  for (int n = 0; n < nt - 1; ++n) {
+    P.sp.cur = fslot(n);
+    P.sp.prev = fslot(n - 1);
+    TRY(launch(ctx, WAVE_KERNEL_STEP, s,
+               [&] { return launch_step(P.R, P.ndim, MODE_BORN_SRC, maps_born, P.sp, P.grid, s); }));
+    if (isrc.n > 0) {
+      const float* row = qd + static_cast<long long>(n) * ns;
+      float* out = slot_ptr(W, P, fslot(n + 1));
+      TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] {
+        return launch_inject_grad(isrc, row, out, W.grad, dmc, 0, nullptr, P.g, P.slabs_x, P.slabs_y,
+                                  P.sp.inv_dt2, s);
+      }));
+    }
+    P.sp.cur = aslot(n);
+    P.sp.prev = aslot(n - 1);
+    TRY(launch(ctx, WAVE_KERNEL_STEP, s,
+               [&] { return launch_step(P.R, P.ndim, MODE_SRC, maps_src, P.sp, P.grid, s); }));
+    if (nr > 0) {
+      float* row = d + static_cast<long long>(n + 1) * nr;
+      const float* du = slot_ptr(W, P, aslot(n + 1));
+      TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_gather(grec, du, row, s); }));
+    }
+  }
+  TRY(finish_out(ctx, dout, s));
+  return WAVE_OK;
+}
+
 // ---------------------------------------------------------------- gradient
 // Storage plan for the forward wavefield of Eq. 3.  A buffer of F snapshot
 // levels first holds the last F levels (nt-F .. nt-1), stored during the
@@ -1503,6 +1578,15 @@ int wave_jacobian_adjoint(wave_context* ctx, const wave_geometry* geom, const fl
   if (nr > 0 && !y) return end_call(ctx, s, fail(ctx, WAVE_ERR_INVALID_ARG, "adjoint source traces are NULL"));
   int rc = gradient_impl(ctx, geom, m, src, q, rec, nullptr, y, grad_out, nullptr, nullptr, d_out, snap_mode, dt, nt,
                          space_order, s);
+  return end_call(ctx, s, rc);
+}
+
+int wave_born(wave_context* ctx, const wave_geometry* geom, const float* m, const float* dm, const wave_points* src,
+              const float* q, const wave_points* rec, float* d_out, float dt, int nt, int space_order, void* stream) {
+  TRY(begin_call(ctx));
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = born_impl(ctx, geom, m, dm, src, q, rec, d_out, dt, nt, space_order, s);
   return end_call(ctx, s, rc);
 }
 

@@ -29,11 +29,15 @@ enum StepMode : int {
   MODE_GRAD_F32 = 4,   // adjoint step + imaging condition, FP32 snapshot read
   MODE_GRAD_BF16 = 5,
   MODE_GRAD_F16 = 6,
-  MODE_COUNT = 7
+  MODE_BORN_SRC = 7,   // background step of Born modelling: + writes S = -dm (new - 2 cur + prev)/dt^2
+  MODE_SRC = 8,        // step with a source field S added to the Laplacian (scattered field)
+  MODE_COUNT = 9
 };
 
 __host__ __device__ constexpr bool mode_is_snap(int m) { return m >= MODE_SNAP_F32 && m <= MODE_SNAP_F16; }
-__host__ __device__ constexpr bool mode_is_grad(int m) { return m >= MODE_GRAD_F32; }
+__host__ __device__ constexpr bool mode_is_grad(int m) { return m >= MODE_GRAD_F32 && m <= MODE_GRAD_F16; }
+// modes that load a third per-point tile through the "g" map (gradient, dm or S)
+__host__ __device__ constexpr bool mode_loads_g(int m) { return mode_is_grad(m) || m == MODE_BORN_SRC || m == MODE_SRC; }
 // snapshot element format: 0 = f32, 1 = bf16, 2 = f16
 __host__ __device__ constexpr int mode_snap_fmt(int m) {
   return m == MODE_SNAP_BF16 || m == MODE_GRAD_BF16 ? 1 : (m == MODE_SNAP_F16 || m == MODE_GRAD_F16 ? 2 : 0);
@@ -91,7 +95,7 @@ struct StepLayout {
   static constexpr int G_OFF = CM_OFF + T::T_ELEMS * 4;
   static constexpr int S_OFF = G_OFF + T::T_ELEMS * 4;
   static constexpr int TILE_BYTES = mode_is_grad(MODE) ? (3 * T::T_ELEMS * 4 + T::T_ELEMS * SNAP_ELEM)
-                                                       : 2 * T::T_ELEMS * 4;
+                                                       : (mode_loads_g(MODE) ? 3 : 2) * T::T_ELEMS * 4;
   static constexpr int P_TX = (T::LEAD ? T::U_BYTES : 0) + TILE_BYTES;  // bytes landing per plane stage
   static constexpr int P_BYTES = PREV_OFF + TILE_BYTES;                   // stage spacing
   static_assert(P_BYTES % 128 == 0, "per-point stage must keep 128-byte alignment");
@@ -124,7 +128,7 @@ struct StepParams {
   // snapshot store (SNAP modes): level base pointer and slab scales
   void* snap_out;
   float* scale_out;
-  // gradient (GRAD modes)
+  // gradient (GRAD modes) or Born source field written by MODE_BORN_SRC
   float* grad;             // [NZ][NY][pitch]
   int snap_level;          // level coordinate in the snapshot store
   const float* scale_in;   // slab scales of that level
@@ -197,6 +201,8 @@ cudaError_t launch_snapshot_store(const GridDims& g, const float* field, void* s
 cudaError_t launch_pack_state(const GridDims& g, const float* field, float* dense, cudaStream_t s);
 cudaError_t launch_unpack_state(const GridDims& g, const float* dense, float* field, cudaStream_t s);
 cudaError_t launch_fill_zero(float* p, long long n, cudaStream_t s);
+// physical field -> computational grid by edge replication (pitched, zero padding columns)
+cudaError_t launch_pad_field(const GridDims& g, const float* phys, float* comp, cudaStream_t s);
 // graph-replay variants: time row = *counter + offset (+1 for the gather)
 cudaError_t launch_inject_counter(const InjectSet& is, const float* q, long long ns, const int* counter, int offset,
                                   float* field, cudaStream_t s);

@@ -76,6 +76,7 @@ _SIGS = {
                                      ctypes.c_int, ctypes.c_int, _P]),
     "wave_jacobian_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_float,
                                              ctypes.c_int, ctypes.c_int, _P]),
+    "wave_born": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, ctypes.c_int, _P]),
     "wave_fd_weights": (ctypes.c_int, [ctypes.c_int, _P]),
     "wave_dt_max": (ctypes.c_double, [ctypes.c_int, _P, ctypes.c_int, ctypes.c_double]),
     "wave_ricker": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
@@ -436,6 +437,24 @@ def wave_jacobian_adjoint(ctx, geom, m, src, q, rec, y, dt, nt, space_order, sna
                                      int(mode), ctypes.c_float(dt), int(nt), int(space_order), st)
     _check(ctx, rc)
     return grad_out
+
+
+def wave_born(ctx, geom, m, dm, src, q, rec, dt, nt, space_order, d_out=None, stream=None):
+    """Linearised data J dm [nt][n_rec] (derivative of wave_forward's data in m)."""
+    m = _f32(m)
+    dm = _f32(dm)
+    g = geom.to_c()
+    ps, src_c = _points(src, geom.ndim)
+    pr, rec_c = _points(rec, geom.ndim)
+    q = _f32(q) if ps.n else None
+    if d_out is None:
+        d_out = _empty_like_kind(m, (nt, pr.n))
+    st = stream if stream is not None else _stream_for(m, dm, q, d_out)
+    rc = lib().wave_born(ctx.handle, ctypes.byref(g), _ptr(m), _ptr(dm), ctypes.byref(ps), _ptr(q),
+                         ctypes.byref(pr), _ptr(d_out) if pr.n else None, ctypes.c_float(dt), int(nt),
+                         int(space_order), st)
+    _check(ctx, rc)
+    return d_out
 
 
 def wave_fd_weights(space_order):
