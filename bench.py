@@ -205,6 +205,18 @@ def measured_traffic(kind, points):
     return None
 
 
+def aggregate(ms_local, units_per_rank, world, dist=None, device="cpu"):
+    """Whole-job throughput of N independent replicas: the max over ranks of the
+    per-step time and value = N * units / that time (units per second)."""
+    ms = float(ms_local)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * units_per_rank / (ms * 1e-3)
+
+
 def hbm_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -339,14 +351,11 @@ def run_ours(args, rank, world, local_rank):
     ctx.set_profiling(False)
     stats = {wave.KERNEL_NAMES[k]: ctx.kernel_stats(k) for k in range(5)}
     launches = ctx.kernel_stats(-1)[0]
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     npts = int(np.prod([s + 2 * w["nbl"] for s in w["shape"]]))
     sweeps = 1 if args.mode == "forward" else 2
     units = sweeps * npts * (nt - 1)
-    value = world * units / (ms * 1e-3) / 1e9
+    ms, value = aggregate(ms, units, world, dist, dev)
+    value /= 1e9
 
     # roofline of the dominant kernel kind
     fmt16 = "bf16" in args.snap or "fp16" in args.snap
@@ -392,11 +401,8 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(args.steps):
             step_host()
         torch.cuda.synchronize()
-        te = (time.perf_counter() - t0) / args.steps
-        if dist:
-            t = torch.tensor([te], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te_ms, _ = aggregate((time.perf_counter() - t0) / args.steps * 1e3, 1.0, world, dist, dev)
+        te = te_ms * 1e-3
         if args.mode == "forward":
             h2d = m_h.nbytes + q_h.nbytes + src_h.nbytes + rec_h.nbytes
             d2h = d_h.nbytes
@@ -454,12 +460,8 @@ def run_serve(args, rank, world, local_rank):
     clk = clocks.stop() if clocks else None
     launches = server.ctx.kernel_stats(-1)[0]
     summ = stats.summary()
-    wall = stats.wall
-    if dist:
-        t = torch.tensor([wall], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        wall = float(t.item())
-    shots = world * len(stats.results) / wall
+    wall_ms, shots = aggregate(stats.wall * 1e3, len(stats.results), world, dist, "cuda")
+    wall = wall_ms * 1e-3
     pts = 0.0
     h2d = d2h = 0
     for r in reqs:

@@ -201,6 +201,18 @@ WAVE_API int wave_gradient(wave_context* ctx, const wave_geometry* geom, const f
                   const float* d_obs, float* grad_out, double* phi_out, float* resid_out,
                   int snap_mode, float dt, int nt, int space_order, void* stream);
 
+/* Multi-shot FWI gradient: the objective of Eq. 2 summed over shots s,
+ * phi = sum_s phi_s, and its gradient sum_s grad_s, for nshots independent
+ * sources on the same model and geometry.  srcs[i] / recs[i] are the points of
+ * shot i, q[i] its traces [nt][n_s,i], d_obs[i] its observed data [nt][n_r,i]
+ * (host or device pointers).  Shots run one after another on the GPU, each
+ * shot's imaging term accumulating into one computational-grid gradient that
+ * is folded once.  Other arguments and errors as wave_gradient. */
+WAVE_API int wave_gradient_shots(wave_context* ctx, const wave_geometry* geom, const float* m, int nshots,
+                                 const wave_points* srcs, const float* const* q, const wave_points* recs,
+                                 const float* const* d_obs, float* grad_out, double* phi_out, int snap_mode,
+                                 float dt, int nt, int space_order, void* stream);
+
 /* Gradient back-propagation for a given receiver-side adjoint source: same as
  * wave_gradient but with the residual replaced by `y` [nt][n_r] (so that
  * grad_out = J^T y, the vector-Jacobian product of the map m -> d used by an

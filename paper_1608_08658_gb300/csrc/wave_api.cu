@@ -1131,10 +1131,12 @@ int plan_storage(wave_context* ctx, Prob& P, int mode, StoragePlan* plan) {
   return WAVE_OK;
 }
 
+// zero_grad / fold: a multi-shot gradient accumulates every shot's imaging
+// term into the same computational-grid buffer and folds once at the end.
 int gradient_impl(wave_context* ctx, const wave_geometry* geom, const float* m, const wave_points* src,
                   const float* q, const wave_points* rec, const float* d_obs, const float* y_given,
                   float* grad_out, double* phi_out, float* resid_out, float* d_out, int snap_mode, float dt, int nt,
-                  int so, cudaStream_t s) {
+                  int so, cudaStream_t s, bool zero_grad = true, bool fold = true) {
   TRY(check_common(ctx, geom, m));
   if (!grad_out) return fail(ctx, WAVE_ERR_INVALID_ARG, "gradient output is NULL");
   Prob P;
@@ -1190,7 +1192,7 @@ int gradient_impl(wave_context* ctx, const wave_geometry* geom, const float* m, 
   W.maps.s = SS.map;
   // forward sweep: checkpoints before each segment start, the tail stored
   CK(cudaMemsetAsync(slot_ptr(W, P, 0), 0, 2 * P.slot_elems * 4, s));
-  CK(cudaMemsetAsync(W.grad, 0, P.slot_elems * 4, s));
+  if (zero_grad) CK(cudaMemsetAsync(W.grad, 0, P.slot_elems * 4, s));
   if (nr > 0) {
     GatherSet grec = gather_set(P, Rr);
     TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_gather(grec, slot_ptr(W, P, fslot(0)), d, s); }));
@@ -1239,9 +1241,11 @@ int gradient_impl(wave_context* ctx, const wave_geometry* geom, const float* m, 
       if (B - 1 >= jlo) TRY(adjoint_grad_steps(ctx, P, W, B - 1, jlo, r, Rr, &SS, A, s));
     }
   }
-  TRY(launch(ctx, WAVE_KERNEL_OTHER, s,
-             [&] { return launch_fold(P.g, W.grad, static_cast<float*>(gout.dev), s); }));
-  TRY(finish_out(ctx, gout, s));
+  if (fold) {
+    TRY(launch(ctx, WAVE_KERNEL_OTHER, s,
+               [&] { return launch_fold(P.g, W.grad, static_cast<float*>(gout.dev), s); }));
+    TRY(finish_out(ctx, gout, s));
+  }
   if (!y_given) TRY(finish_out(ctx, rout, s));
   TRY(finish_out(ctx, dout, s));
   CK(cudaMemcpyAsync(ctx->h_phi, ctx->d_phi, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1578,6 +1582,27 @@ int wave_jacobian_adjoint(wave_context* ctx, const wave_geometry* geom, const fl
   if (nr > 0 && !y) return end_call(ctx, s, fail(ctx, WAVE_ERR_INVALID_ARG, "adjoint source traces are NULL"));
   int rc = gradient_impl(ctx, geom, m, src, q, rec, nullptr, y, grad_out, nullptr, nullptr, d_out, snap_mode, dt, nt,
                          space_order, s);
+  return end_call(ctx, s, rc);
+}
+
+int wave_gradient_shots(wave_context* ctx, const wave_geometry* geom, const float* m, int nshots,
+                        const wave_points* srcs, const float* const* q, const wave_points* recs,
+                        const float* const* d_obs, float* grad_out, double* phi_out, int snap_mode, float dt, int nt,
+                        int space_order, void* stream) {
+  TRY(begin_call(ctx));
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (nshots < 1 || !srcs || !recs || !q || !d_obs)
+    return end_call(ctx, s, fail(ctx, WAVE_ERR_INVALID_ARG, "need nshots >= 1 and per-shot arrays"));
+  double total = 0.0;
+  int rc = WAVE_OK;
+  for (int i = 0; i < nshots && rc == WAVE_OK; ++i) {
+    double phi = 0.0;
+    rc = gradient_impl(ctx, geom, m, &srcs[i], q[i], &recs[i], d_obs[i], nullptr, grad_out, &phi, nullptr, nullptr,
+                       snap_mode, dt, nt, space_order, s, i == 0, i == nshots - 1);
+    total += phi;
+  }
+  if (rc == WAVE_OK && phi_out) *phi_out = total;
   return end_call(ctx, s, rc);
 }
 

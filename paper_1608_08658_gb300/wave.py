@@ -76,6 +76,8 @@ _SIGS = {
                                      ctypes.c_int, ctypes.c_int, _P]),
     "wave_jacobian_adjoint": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_float,
                                              ctypes.c_int, ctypes.c_int, _P]),
+    "wave_gradient_shots": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_int, _P]),
     "wave_born": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, ctypes.c_int, _P]),
     "wave_fd_weights": (ctypes.c_int, [ctypes.c_int, _P]),
     "wave_dt_max": (ctypes.c_double, [ctypes.c_int, _P, ctypes.c_int, ctypes.c_double]),
@@ -437,6 +439,35 @@ def wave_jacobian_adjoint(ctx, geom, m, src, q, rec, y, dt, nt, space_order, sna
                                      int(mode), ctypes.c_float(dt), int(nt), int(space_order), st)
     _check(ctx, rc)
     return grad_out
+
+
+def wave_gradient_shots(ctx, geom, m, shots, dt, nt, space_order, snap_mode="auto", grad_out=None, stream=None):
+    """(sum of gradients, sum of objectives) over ``shots`` = [(src, q, rec, d_obs), ...]."""
+    mode = SNAP_MODES[snap_mode] if isinstance(snap_mode, str) else int(snap_mode)
+    m = _f32(m)
+    g = geom.to_c()
+    n = len(shots)
+    srcs = (c_points * n)()
+    recs = (c_points * n)()
+    qs = (ctypes.c_void_p * n)()
+    obs = (ctypes.c_void_p * n)()
+    keep = []
+    for i, (src, q, rec, d_obs) in enumerate(shots):
+        ps, sc = _points(src, geom.ndim)
+        pr, rc_ = _points(rec, geom.ndim)
+        qf, df = _f32(q), _f32(d_obs)
+        keep += [sc, rc_, qf, df]
+        srcs[i], recs[i] = ps, pr
+        qs[i], obs[i] = _ptr(qf), _ptr(df)
+    if grad_out is None:
+        grad_out = _empty_like_kind(m, geom.phys_array_shape)
+    phi = ctypes.c_double()
+    st = stream if stream is not None else _stream_for(m, grad_out)
+    rc = lib().wave_gradient_shots(ctx.handle, ctypes.byref(g), _ptr(m), n, srcs, qs, recs, obs, _ptr(grad_out),
+                                   ctypes.byref(phi), int(mode), ctypes.c_float(dt), int(nt), int(space_order), st)
+    _check(ctx, rc)
+    del keep
+    return grad_out, phi.value
 
 
 def wave_born(ctx, geom, m, dm, src, q, rec, dt, nt, space_order, d_out=None, stream=None):

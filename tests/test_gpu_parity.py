@@ -162,6 +162,39 @@ def test_gradient_under_tight_budgets(ctx):
     assert 1 in seen and max(seen) >= 2
 
 
+def test_multi_shot_gradient_is_the_sum(ctx):
+    """Eq. 2 summed over shots: the multi-shot call equals the sum of single-shot
+    gradients and objectives, and the oracle's sum."""
+    og, m, dt, nt, so, _, _, rec = small3d(8, nt=50)
+    _, geom = geometries(og)
+    rng = np.random.default_rng(23)
+    lo = np.array(og.origin)
+    hi = lo + (np.array(og.shape) - 1) * np.array(og.spacing)
+    shots = []
+    for i in range(3):
+        src = (lo + rng.uniform(0.2, 0.8, size=(1, 3)) * (hi - lo)).astype(np.float32)
+        q = (rng.standard_normal((nt, 1)) * 1e2).astype(np.float32)
+        d_obs = oracle.wave.forward(og, m * 1.02, dt, nt, so, q, src, rec).d.astype(np.float32)
+        shots.append((src, q, rec, d_obs))
+    g, phi = wave.wave_gradient_shots(ctx, geom, _dev(m), [(s, _dev(q), r, _dev(d)) for s, q, r, d in shots], dt, nt,
+                                      so, snap_mode="full_fp32")
+    g = g.cpu().numpy().astype(np.float64)
+    g_sum = np.zeros_like(g)
+    phi_sum = 0.0
+    g_ref = np.zeros_like(g)
+    phi_ref = 0.0
+    for src, q, rec_, d_obs in shots:
+        gi, pi = wave.wave_gradient(ctx, geom, _dev(m), src, _dev(q), rec_, _dev(d_obs), dt, nt, so,
+                                    snap_mode="full_fp32")
+        g_sum += gi.cpu().numpy()
+        phi_sum += pi
+        gr, pr = oracle.wave.gradient(og, m, dt, nt, so, q, src, rec_, d_obs)
+        g_ref += gr
+        phi_ref += pr
+    assert rel_l2(g, g_sum) <= 1e-5 and abs(phi - phi_sum) <= 1e-12 * phi_sum
+    assert rel_l2(g, g_ref) <= 5e-4 and abs(phi - phi_ref) <= 1e-4 * phi_ref
+
+
 def test_jacobian_adjoint_matches_gradient(ctx):
     og, m, dt, nt, so, src, q, rec = small2d(6)
     _, geom = geometries(og)
