@@ -252,8 +252,8 @@ __global__ void snapshot_store_kernel(GridDims g, const float* __restrict__ fiel
     if (ok) *reinterpret_cast<float4*>(static_cast<float*>(snap) + idx) = v;
     return;
   }
-  float amax = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
-  for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+  const float lmax = fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w)));
+  const float amax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(lmax)));
   const float s = dev::slab_scale(amax);
   const float is = dev::slab_inv_scale(s);
   if (ok) {

@@ -48,9 +48,11 @@ int step_smem_bytes(int R, int ndim, int mode) {
 int step_threads() { return StepTraits<1, 3>::NTHREADS; }
 int step_bx() { return StepTraits<1, 3>::BX; }
 int step_by(int R, int ndim) {
-  (void)R;
-  (void)ndim;
-  return StepTraits<1, 3>::BY;
+  switch (ndim == 3 ? R : 0) {
+    case 7: return StepTraits<7, 3>::BY;
+    case 8: return StepTraits<8, 3>::BY;
+    default: return StepTraits<1, 3>::BY;
+  }
 }
 int step_hx(int R) { return R <= 4 ? 4 : 8; }
 

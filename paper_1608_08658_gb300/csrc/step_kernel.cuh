@@ -87,9 +87,6 @@ __device__ __forceinline__ float4 load_snap4_smem(const unsigned char* p, float 
   return make_float4(a.x * s, a.y * s, b.x * s, b.y * s);
 }
 
-// Resident CTAs per SM requested from the register allocator: 3 up to radius
-// 4, 2 above (the lead-plane ring keeps the shared memory of radius 7-8
-// within two CTAs per SM).
 #ifndef WAVE_STEP_MINB
 #define WAVE_STEP_MINB 3
 #endif
@@ -98,8 +95,17 @@ __device__ __forceinline__ float4 load_snap4_smem(const unsigned char* p, float 
 #endif
 
 
+// Resident CTAs per SM asked of the register allocator.  The register file is
+// split over the SM's four sub-partitions, so the cap follows the warps per
+// sub-partition: 3 CTAs of 9 warps (7 per sub-partition) leave 72 registers,
+// 2 CTAs of 9 warps (5) leave 96, 2 CTAs of 8 warps (4) leave 128.
 template <int R, int NDIM, int MODE>
-__global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_STEP_MINB : WAVE_STEP_MINB_HI))
+struct StepRegs {
+  static constexpr int kMinBlocks = (R <= 4 && !mode_is_grad(MODE)) ? WAVE_STEP_MINB : WAVE_STEP_MINB_HI;
+};
+
+template <int R, int NDIM, int MODE>
+__global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepRegs<R, NDIM, MODE>::kMinBlocks))
     step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
                 const __grid_constant__ CUtensorMap tm_cm, const __grid_constant__ CUtensorMap tm_g,
                 const __grid_constant__ CUtensorMap tm_s, const StepParams p) {
@@ -204,7 +210,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
   }
 
   // ------------------------------------------------------------------ consumers
-  const int ty = tid >> 4;  // row of the tile, 0..15
+  const int ty = tid >> 4;  // row of the tile, 0..BY-1
   const int tx = tid & 15;  // quad of 4 x points
   const int gx = x0 + 4 * tx;
   const int gy = y0 + ty;
@@ -270,16 +276,29 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
 
   const long long plane_elems = static_cast<long long>(p.NY) * p.pitch;
   long long idx = static_cast<long long>(z0) * plane_elems + static_cast<long long>(gy) * p.pitch + gx;
+  // 16-bit snapshots read by the imaging condition: this thread's slab scale
+  // for plane z0 + j is scale_ptr[j * scale_plane], prefetched a plane ahead
+  const long long scale_plane = static_cast<long long>(p.slabs_y) * p.slabs_x;
+  const float* scale_ptr = nullptr;
+  float scale_next = 1.f;
+  if constexpr (mode_is_grad(MODE) && FMT != 0) {
+    scale_ptr = p.scale_in + (static_cast<long long>(z0) * p.slabs_y + (min(gy, p.NY - 1) >> 1)) * p.slabs_x +
+                blockIdx.x;
+    scale_next = __ldg(scale_ptr);
+  }
   float* const out_base = p.fields + p.prev * p.slot_elems;
   int j = 0;
+  // ring positions of output plane j: plane z+R has sequence j+2RZ in the
+  // queue-feed ring, the centre plane j+RZ, the per-point tiles j
+  int ring_un = (2 * RZ) % T::NSU, ring_ps = 0;
+  uint32_t phase_un = ((2 * RZ) / T::NSU) & 1, phase_ps = 0;
 
   // One output plane z = z0 + j.
   auto plane = [&]() -> bool {
-    const int sn = j + 2 * RZ;  // sequence number of plane z+R
-    const int sc = j + RZ;      // sequence number of the centre plane z
-    const int un = sn % T::NSU;
-    const int uc = sc % T::NSU;
-    bool good = mbar_wait_bounded(&fullU[un], (sn / T::NSU) & 1, abort_flag, kWaitLimitNs);
+    // ring slots and phases advance by one per plane (no division in the loop)
+    const int un = ring_un, ps = ring_ps;
+    const int uc = un >= RZ ? un - RZ : un + T::NSU - RZ;  // slot of the centre plane
+    bool good = mbar_wait_bounded(&fullU[un], phase_un, abort_flag, kWaitLimitNs);
     if (!__all_sync(0xffffffffu, good)) return false;
     q[2 * RZ] = lds4(Ubase + un * (T::Q_STRIDE / 4) + qofs);
     if constexpr (T::LEAD) {
@@ -287,10 +306,9 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
       if (lane == 0) mbar_arrive(&emptyU[un]);
     }
     const float4 c = q[RZ];
-    const int ps = j % T::NSP;
     if constexpr (T::LEAD) {
       // the centre halo box arrives with the per-point tiles
-      good = mbar_wait_bounded(&fullP[ps], (j / T::NSP) & 1, abort_flag, kWaitLimitNs);
+      good = mbar_wait_bounded(&fullP[ps], phase_ps, abort_flag, kWaitLimitNs);
       if (!__all_sync(0xffffffffu, good)) return false;
     }
     const float* Uc = T::LEAD ? reinterpret_cast<const float*>(Pbase + ps * L::P_BYTES + L::HALO_OFF) + lofs
@@ -351,7 +369,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
       }
     }
     if constexpr (!T::LEAD) {
-      good = mbar_wait_bounded(&fullP[ps], (j / T::NSP) & 1, abort_flag, kWaitLimitNs);
+      good = mbar_wait_bounded(&fullP[ps], phase_ps, abort_flag, kWaitLimitNs);
       if (!__all_sync(0xffffffffu, good)) return false;
     }
     const unsigned char* Pst = Pbase + ps * L::P_BYTES;
@@ -391,9 +409,10 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
       if constexpr (FMT == 0) {
         if (store_ok) store_snap4<0>(p.snap_out, idx, c, 1.f);
       } else {
-        float amax = fmaxf(fmaxf(fabsf(c.x), fabsf(c.y)), fmaxf(fabsf(c.z), fabsf(c.w)));
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+        // slab max |u|: non-negative floats order like their bit patterns, so
+        // one integer warp reduction gives it
+        const float lmax = fmaxf(fmaxf(fabsf(c.x), fabsf(c.y)), fmaxf(fabsf(c.z), fabsf(c.w)));
+        const float amax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(lmax)));
         const float s = slab_scale(amax);
         if (store_ok) store_snap4<FMT>(p.snap_out, idx, c, slab_inv_scale(s));
         if (lane == 0 && gy < p.NY)
@@ -413,8 +432,9 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
     if constexpr (mode_is_grad(MODE)) {
       float s = 1.f;
       if constexpr (FMT != 0) {
-        const int sy = min(gy, p.NY - 1) >> 1;
-        s = __ldg(p.scale_in + (static_cast<long long>(gz) * p.slabs_y + sy) * p.slabs_x + blockIdx.x);
+        // slab scale of this plane was loaded one plane ahead
+        s = scale_next;
+        if (j + 1 < nP) scale_next = __ldg(scale_ptr + (j + 1) * scale_plane);
       }
       const float4 u = load_snap4_smem<FMT>(Pst + L::S_OFF + (ty * T::BX + 4 * tx) * L::SNAP_ELEM, s);
       float4 g = *reinterpret_cast<const float4*>(Pst + L::G_OFF + tofs);
@@ -439,6 +459,14 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (R <= 4 ? WAVE_
       if (!ok) break;
 #pragma unroll
       for (int i = 0; i < 2 * RZ; ++i) q[i] = q[i + 1];
+      if (++ring_un == T::NSU) {
+        ring_un = 0;
+        phase_un ^= 1u;
+      }
+      if (++ring_ps == T::NSP) {
+        ring_ps = 0;
+        phase_ps ^= 1u;
+      }
     }
   }
   if (!ok && lane == 0) {

@@ -56,11 +56,17 @@ constexpr int kSlabY = 2;
 #ifndef WAVE_LEAD_MIN_R
 #define WAVE_LEAD_MIN_R 7
 #endif
+#ifndef WAVE_BY14_MIN_R
+#define WAVE_BY14_MIN_R 8
+#endif
 
 template <int R, int NDIM>
 struct StepTraits {
   static constexpr int BX = 64;                   // x outputs per CTA (16 threads x 4)
-  static constexpr int BY = 16;                   // axis-1 outputs per CTA (one row per 16 threads)
+  // axis-1 outputs per CTA (one row per 16 threads, two rows per warp); 3D
+  // radius 8 uses 14 rows so that a CTA has 8 warps and two CTAs fit the
+  // register file at 128 registers per thread
+  static constexpr int BY = (NDIM == 3 && R >= WAVE_BY14_MIN_R) ? 14 : 16;
   static constexpr int HX = (R <= 4) ? 4 : 8;     // x halo, rounded to 16 bytes for TMA
   static constexpr int RZ = (NDIM == 3) ? R : 0;  // halo along the streamed axis
   static constexpr int PF = (NDIM == 3) ? 2 : 0;  // extra planes prefetched ahead
@@ -80,7 +86,7 @@ struct StepTraits {
   static constexpr int Q_STRIDE = LEAD ? T_ELEMS * 4 : U_STRIDE;
   // per-plane ring: per-point tiles (+ the centre halo box in the lead design)
   static constexpr int NSP = (NDIM == 3) ? 3 : 1;
-  static constexpr int NCW = 8;                   // consumer warps
+  static constexpr int NCW = BY / 2;              // consumer warps
   static constexpr int NTHREADS = (NCW + 1) * 32; // + one producer warp
 };
 
@@ -147,6 +153,7 @@ struct StepMaps {
 
 cudaError_t launch_step(int R, int ndim, int mode, const StepMaps& maps, const StepParams& p,
                         dim3 grid, cudaStream_t stream);
+// NOTE: step_by() must agree with StepTraits<R, NDIM>::BY.
 int step_smem_bytes(int R, int ndim, int mode);
 int step_threads();
 int step_bx();
