@@ -1,5 +1,5 @@
 // Runtime dispatch of the stencil step over the stencil radius.
-#include "step_kernel.cuh"
+#include "step_launch.cuh"
 
 namespace wave {
 
@@ -45,13 +45,19 @@ int step_smem_bytes(int R, int ndim, int mode) {
   }
 }
 
-int step_threads() { return StepTraits<1, 3>::NTHREADS; }
 int step_bx() { return StepTraits<1, 3>::BX; }
 int step_by(int R, int ndim) {
-  switch (ndim == 3 ? R : 0) {
+  if (ndim != 3) return StepTraits<1, 2>::BY;
+  switch (R) {
+    case 1: return StepTraits<1, 3>::BY;
+    case 2: return StepTraits<2, 3>::BY;
+    case 3: return StepTraits<3, 3>::BY;
+    case 4: return StepTraits<4, 3>::BY;
+    case 5: return StepTraits<5, 3>::BY;
+    case 6: return StepTraits<6, 3>::BY;
     case 7: return StepTraits<7, 3>::BY;
     case 8: return StepTraits<8, 3>::BY;
-    default: return StepTraits<1, 3>::BY;
+    default: return -1;
   }
 }
 int step_hx(int R) { return R <= 4 ? 4 : 8; }

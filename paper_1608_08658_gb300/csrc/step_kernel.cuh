@@ -26,6 +26,7 @@
 #include <cuda_fp16.h>
 
 
+
 #include "ptx.cuh"
 #include "wave_internal.h"
 
@@ -87,25 +88,14 @@ __device__ __forceinline__ float4 load_snap4_smem(const unsigned char* p, float 
   return make_float4(a.x * s, a.y * s, b.x * s, b.y * s);
 }
 
-#ifndef WAVE_STEP_MINB
-#define WAVE_STEP_MINB 3
-#endif
-#ifndef WAVE_STEP_MINB_HI
-#define WAVE_STEP_MINB_HI 2
-#endif
-
-
-// Resident CTAs per SM asked of the register allocator.  The register file is
-// split over the SM's four sub-partitions, so the cap follows the warps per
-// sub-partition: 3 CTAs of 9 warps (7 per sub-partition) leave 72 registers,
-// 2 CTAs of 9 warps (5) leave 96, 2 CTAs of 8 warps (4) leave 128.
-template <int R, int NDIM, int MODE>
-struct StepRegs {
-  static constexpr int kMinBlocks = (R <= 4 && !mode_is_grad(MODE)) ? WAVE_STEP_MINB : WAVE_STEP_MINB_HI;
+// compile-time plane offset inside a group of planes
+template <int V>
+struct IntC {
+  static constexpr int value = V;
 };
 
 template <int R, int NDIM, int MODE>
-__global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepRegs<R, NDIM, MODE>::kMinBlocks))
+__global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepLayout<R, NDIM, MODE>::MIN_BLOCKS))
     step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
                 const __grid_constant__ CUtensorMap tm_cm, const __grid_constant__ CUtensorMap tm_g,
                 const __grid_constant__ CUtensorMap tm_s, const StepParams p) {
@@ -118,8 +108,8 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepRegs<R, ND
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
   uint64_t* fullU = reinterpret_cast<uint64_t*>(smem);
-  uint64_t* emptyU = fullU + T::NSU;
-  uint64_t* fullP = emptyU + T::NSU;
+  uint64_t* emptyU = fullU + L::NSU;
+  uint64_t* fullP = emptyU + L::NSU;
   uint64_t* emptyP = fullP + T::NSP;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(emptyP + T::NSP);
   float* Ubase = reinterpret_cast<float*>(smem + L::U_OFF);
@@ -137,7 +127,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepRegs<R, ND
   if (nP <= 0) return;
 
   if (tid == 0) {
-    for (int i = 0; i < T::NSU; ++i) {
+    for (int i = 0; i < L::NSU; ++i) {
       mbar_init(&fullU[i], 1);
       mbar_init(&emptyU[i], T::NCW);
     }
@@ -161,14 +151,14 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepRegs<R, ND
       int issuedU = 0, issuedP = 0;
       bool ok = true;
       for (int s = 0; s < nU; ++s) {
-        const int slot = s % T::NSU;
-        if (s >= T::NSU) ok = mbar_wait_bounded(&emptyU[slot], ((s / T::NSU) - 1) & 1, abort_flag, kWaitLimitNs);
+        const int slot = s % L::NSU;
+        if (s >= L::NSU) ok = mbar_wait_bounded(&emptyU[slot], ((s / L::NSU) - 1) & 1, abort_flag, kWaitLimitNs);
         if (!ok) break;
-        mbar_arrive_expect_tx(&fullU[slot], T::Q_BYTES);
-        if constexpr (T::LEAD)
-          tma_load_4d(Ubase + slot * (T::Q_STRIDE / 4), &tm_p, x0, y0, z0 - RZ + s, p.cur, &fullU[slot]);
+        mbar_arrive_expect_tx(&fullU[slot], L::Q_BYTES);
+        if constexpr (L::LEAD)
+          tma_load_4d(Ubase + slot * (L::Q_STRIDE / 4), &tm_p, x0, y0, z0 - RZ + s, p.cur, &fullU[slot]);
         else
-          tma_load_4d(Ubase + slot * (T::Q_STRIDE / 4), &tm_u, x0 - T::HX, y0 - R, z0 - RZ + s, p.cur, &fullU[slot]);
+          tma_load_4d(Ubase + slot * (L::Q_STRIDE / 4), &tm_u, x0 - T::HX, y0 - R, z0 - RZ + s, p.cur, &fullU[slot]);
         issuedU = s + 1;
         if (s >= 2 * RZ) {
           const int j = s - 2 * RZ;
@@ -177,7 +167,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepRegs<R, ND
           if (!ok) break;
           unsigned char* pd = Pbase + ps * L::P_BYTES;
           mbar_arrive_expect_tx(&fullP[ps], L::P_TX);
-          if constexpr (T::LEAD)
+          if constexpr (L::LEAD)
             tma_load_4d(pd + L::HALO_OFF, &tm_u, x0 - T::HX, y0 - R, z0 + j, p.cur, &fullP[ps]);
           tma_load_4d(pd + L::PREV_OFF, &tm_p, x0, y0, z0 + j, p.prev, &fullP[ps]);
           tma_load_3d(pd + L::CM_OFF, &tm_cm, x0, y0, z0 + j, &fullP[ps]);
@@ -192,10 +182,10 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepRegs<R, ND
       }
       if (*abort_flag) {
         // let every copy this thread issued land before the CTA exits
-        for (int slot = 0; slot < T::NSU; ++slot) {
+        for (int slot = 0; slot < L::NSU; ++slot) {
           if (issuedU > slot) {
-            const int last = slot + T::NSU * ((issuedU - 1 - slot) / T::NSU);
-            mbar_wait_bounded(&fullU[slot], (last / T::NSU) & 1, nullptr, kWaitLimitNs);
+            const int last = slot + L::NSU * ((issuedU - 1 - slot) / L::NSU);
+            mbar_wait_bounded(&fullU[slot], (last / L::NSU) & 1, nullptr, kWaitLimitNs);
           }
         }
         for (int slot = 0; slot < T::NSP; ++slot) {
@@ -217,7 +207,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepRegs<R, ND
   const bool store_ok = (gx < p.NX) && (gy < p.NY);
   const int lofs = (R + ty) * T::UW + T::HX + 4 * tx;  // centre of this quad in a halo box
   const int tofs = (ty * T::BX + 4 * tx) * 4;          // byte offset of this quad in a tile
-  const int qofs = T::LEAD ? tofs / 4 : lofs;           // this quad in a queue-feed stage
+  const int qofs = L::LEAD ? tofs / 4 : lofs;           // this quad in a queue-feed stage
 
   // sponge along x (per point) and axis 1 (per row)
   const float ey = sponge_term(gy, p.NY, p.nbly, p.emy);
@@ -229,7 +219,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepRegs<R, ND
 
   // Coefficients as packed pairs (loop invariant) up to radius 6; above, the
   // 6R pairs would cost too many registers, so the multiply takes the scalar
-  // coefficient from the constant bank and only the sums stay packed.
+  // coefficient from the parameter bank and only the sums stay packed.
   constexpr bool PCOEF = R <= 6;
   constexpr int NPC = PCOEF ? R : 1;
   const float2 c0v = make_float2(p.c0, p.c0);
@@ -241,21 +231,25 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepRegs<R, ND
   }
 #pragma unroll
   for (int k = 0; k < (PCOEF ? RZ : 0); ++k) czv[k] = make_float2(p.cz[k], p.cz[k]);
-  // acc += c * (a + b) on a packed pair
-  auto tap2 = [&](float2& acc, const float2& cv, float cs, const float2& a, const float2& b) {
+  // acc += c_{axis,k} * (a + b) on a packed pair (axis 0 = x, 1 = axis 1, 2 = axis 2)
+  auto tap2 = [&](float2& acc, int axis, int k, const float2& a, const float2& b) {
     const float2 sum = __fadd2_rn(a, b);
     if constexpr (PCOEF) {
-      acc = __ffma2_rn(cv, sum, acc);
+      acc = __ffma2_rn(axis == 0 ? cxv[k] : (axis == 1 ? cyv[k] : czv[k]), sum, acc);
     } else {
+      const float cs = axis == 0 ? p.cx[k] : (axis == 1 ? p.cy[k] : p.cz[k]);
       acc.x = fmaf(cs, sum.x, acc.x);
       acc.y = fmaf(cs, sum.y, acc.y);
     }
   };
 
-  // Register queue of the centre level along the streamed axis: before output
-  // plane z, q[0 .. 2RZ-1] hold planes z-RZ .. z+RZ-1; plane z+RZ lands in
-  // q[2RZ] and the queue moves down by one afterwards.
-  constexpr int NQ = 2 * RZ + 1;
+  // Register queue of the centre level along the streamed axis.  Planes are
+  // processed in groups of QU: before a group starting at output plane z,
+  // q[0 .. 2RZ-1] hold planes z-RZ .. z+RZ-1; plane z+u+RZ of the group lands
+  // in q[2RZ+u], and the queue moves down by QU after the group (by one after
+  // a single plane).
+  constexpr int QU = L::QU;
+  constexpr int NQ = 2 * RZ + QU;
   float4 q[NQ];
 #pragma unroll
   for (int i = 0; i < NQ; ++i) q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -263,12 +257,12 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepRegs<R, ND
   bool ok = true;
 #pragma unroll
   for (int s = 0; s < 2 * RZ; ++s) {
-    const int slot = s % T::NSU;
-    ok = mbar_wait_bounded(&fullU[slot], (s / T::NSU) & 1, abort_flag, kWaitLimitNs);
+    const int slot = s % L::NSU;
+    ok = mbar_wait_bounded(&fullU[slot], (s / L::NSU) & 1, abort_flag, kWaitLimitNs);
     ok = __all_sync(0xffffffffu, ok);
     if (!ok) break;
-    q[s] = lds4(Ubase + slot * (T::Q_STRIDE / 4) + qofs);
-    if (T::LEAD || s < RZ) {
+    q[s] = lds4(Ubase + slot * (L::Q_STRIDE / 4) + qofs);
+    if (L::LEAD || s < RZ) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&emptyU[slot]);
     }
@@ -290,46 +284,46 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepRegs<R, ND
   int j = 0;
   // ring positions of output plane j: plane z+R has sequence j+2RZ in the
   // queue-feed ring, the centre plane j+RZ, the per-point tiles j
-  int ring_un = (2 * RZ) % T::NSU, ring_ps = 0;
-  uint32_t phase_un = ((2 * RZ) / T::NSU) & 1, phase_ps = 0;
+  int ring_un = (2 * RZ) % L::NSU, ring_ps = 0;
+  uint32_t phase_un = ((2 * RZ) / L::NSU) & 1, phase_ps = 0;
 
-  // One output plane z = z0 + j.
-  auto plane = [&]() -> bool {
-    // ring slots and phases advance by one per plane (no division in the loop)
+  // One output plane z = z0 + j, taking its queue entries at offset O.
+  auto plane = [&](auto oc) -> bool {
+    constexpr int O = decltype(oc)::value;
     const int un = ring_un, ps = ring_ps;
-    const int uc = un >= RZ ? un - RZ : un + T::NSU - RZ;  // slot of the centre plane
+    const int uc = un >= RZ ? un - RZ : un + L::NSU - RZ;  // slot of the centre plane
     bool good = mbar_wait_bounded(&fullU[un], phase_un, abort_flag, kWaitLimitNs);
     if (!__all_sync(0xffffffffu, good)) return false;
-    q[2 * RZ] = lds4(Ubase + un * (T::Q_STRIDE / 4) + qofs);
-    if constexpr (T::LEAD) {
+    q[O + 2 * RZ] = lds4(Ubase + un * (L::Q_STRIDE / 4) + qofs);
+    if constexpr (L::LEAD) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&emptyU[un]);
     }
-    const float4 c = q[RZ];
-    if constexpr (T::LEAD) {
+    const float4 c = q[O + RZ];
+    if constexpr (L::LEAD) {
       // the centre halo box arrives with the per-point tiles
       good = mbar_wait_bounded(&fullP[ps], phase_ps, abort_flag, kWaitLimitNs);
       if (!__all_sync(0xffffffffu, good)) return false;
     }
-    const float* Uc = T::LEAD ? reinterpret_cast<const float*>(Pbase + ps * L::P_BYTES + L::HALO_OFF) + lofs
-                              : Ubase + uc * (T::Q_STRIDE / 4) + lofs;
+    const float* Uc = L::LEAD ? reinterpret_cast<const float*>(Pbase + ps * L::P_BYTES + L::HALO_OFF) + lofs
+                              : Ubase + uc * (L::Q_STRIDE / 4) + lofs;
 
     // Laplacian on two packed pairs (points 0,1 and 2,3 of the quad)
     float2 la = __fmul2_rn(c0v, make_float2(c.x, c.y));
     float2 lb = __fmul2_rn(c0v, make_float2(c.z, c.w));
 #pragma unroll
     for (int k = 1; k <= RZ; ++k) {
-      const float4 a = q[RZ - k];
-      const float4 b = q[RZ + k];
-      tap2(la, czv[PCOEF ? k - 1 : 0], p.cz[k - 1], make_float2(a.x, a.y), make_float2(b.x, b.y));
-      tap2(lb, czv[PCOEF ? k - 1 : 0], p.cz[k - 1], make_float2(a.z, a.w), make_float2(b.z, b.w));
+      const float4 a = q[O + RZ - k];
+      const float4 b = q[O + RZ + k];
+      tap2(la, 2, k - 1, make_float2(a.x, a.y), make_float2(b.x, b.y));
+      tap2(lb, 2, k - 1, make_float2(a.z, a.w), make_float2(b.z, b.w));
     }
 #pragma unroll
     for (int k = 1; k <= R; ++k) {
       const float4 a = lds4(Uc - k * T::UW);
       const float4 b = lds4(Uc + k * T::UW);
-      tap2(la, cyv[PCOEF ? k - 1 : 0], p.cy[k - 1], make_float2(a.x, a.y), make_float2(b.x, b.y));
-      tap2(lb, cyv[PCOEF ? k - 1 : 0], p.cy[k - 1], make_float2(a.z, a.w), make_float2(b.z, b.w));
+      tap2(la, 1, k - 1, make_float2(a.x, a.y), make_float2(b.x, b.y));
+      tap2(lb, 1, k - 1, make_float2(a.z, a.w), make_float2(b.z, b.w));
     }
     {
       constexpr int NH = T::HX / 4;  // halo quads per side
@@ -356,10 +350,8 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepRegs<R, ND
         constexpr int H = T::HX;
         if (k % 2 == 0) {
           // even offsets keep the pairs register-aligned
-          tap2(la, cxv[PCOEF ? k - 1 : 0], p.cx[k - 1], make_float2(v[H - k], v[H + 1 - k]),
-               make_float2(v[H + k], v[H + 1 + k]));
-          tap2(lb, cxv[PCOEF ? k - 1 : 0], p.cx[k - 1], make_float2(v[H + 2 - k], v[H + 3 - k]),
-               make_float2(v[H + 2 + k], v[H + 3 + k]));
+          tap2(la, 0, k - 1, make_float2(v[H - k], v[H + 1 - k]), make_float2(v[H + k], v[H + 1 + k]));
+          tap2(lb, 0, k - 1, make_float2(v[H + 2 - k], v[H + 3 - k]), make_float2(v[H + 2 + k], v[H + 3 + k]));
         } else {
           la.x = fmaf(p.cx[k - 1], v[H + 0 - k] + v[H + 0 + k], la.x);
           la.y = fmaf(p.cx[k - 1], v[H + 1 - k] + v[H + 1 + k], la.y);
@@ -368,7 +360,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepRegs<R, ND
         }
       }
     }
-    if constexpr (!T::LEAD) {
+    if constexpr (!L::LEAD) {
       good = mbar_wait_bounded(&fullP[ps], phase_ps, abort_flag, kWaitLimitNs);
       if (!__all_sync(0xffffffffu, good)) return false;
     }
@@ -447,26 +439,44 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepRegs<R, ND
 
     __syncwarp();
     if (lane == 0) {
-      if constexpr (!T::LEAD) mbar_arrive(&emptyU[uc]);
+      if constexpr (!L::LEAD) mbar_arrive(&emptyU[uc]);
       mbar_arrive(&emptyP[ps]);
     }
     return true;
   };
 
-  if (ok) {
-    for (; j < nP; ++j, idx += plane_elems) {
-      ok = plane();
+  // ring slots and phases advance by one per plane (no division in the loop)
+  auto advance = [&]() {
+    ++j;
+    idx += plane_elems;
+    if (++ring_un == L::NSU) {
+      ring_un = 0;
+      phase_un ^= 1u;
+    }
+    if (++ring_ps == T::NSP) {
+      ring_ps = 0;
+      phase_ps ^= 1u;
+    }
+  };
+  if (ok && QU == 2) {
+    while (j + 2 <= nP) {
+      ok = plane(IntC<0>{});
       if (!ok) break;
+      advance();
+      ok = plane(IntC<QU - 1>{});
+      if (!ok) break;
+      advance();
+#pragma unroll
+      for (int i = 0; i < 2 * RZ; ++i) q[i] = q[i + QU];
+    }
+  }
+  if (ok) {
+    while (j < nP) {
+      ok = plane(IntC<0>{});
+      if (!ok) break;
+      advance();
 #pragma unroll
       for (int i = 0; i < 2 * RZ; ++i) q[i] = q[i + 1];
-      if (++ring_un == T::NSU) {
-        ring_un = 0;
-        phase_un ^= 1u;
-      }
-      if (++ring_ps == T::NSP) {
-        ring_ps = 0;
-        phase_ps ^= 1u;
-      }
     }
   }
   if (!ok && lane == 0) {
@@ -477,62 +487,4 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepRegs<R, ND
 
 }  // namespace dev
 
-// Host launcher for one radius; instantiated once per step_r<R>.cu.
-template <int R, int NDIM, int MODE>
-static cudaError_t launch_one(const StepMaps& maps, const StepParams& p, dim3 grid, cudaStream_t stream) {
-  using T = StepTraits<R, NDIM>;
-  using L = StepLayout<R, NDIM, MODE>;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(dev::step_kernel<R, NDIM, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
-  dev::step_kernel<R, NDIM, MODE><<<grid, T::NTHREADS, L::SMEM, stream>>>(maps.u, maps.p, maps.cm, maps.g, maps.s, p);
-  return cudaGetLastError();
-}
-
-template <int R, int NDIM>
-static cudaError_t launch_modes(int mode, const StepMaps& maps, const StepParams& p, dim3 grid, cudaStream_t s) {
-  switch (mode) {
-    case MODE_PLAIN: return launch_one<R, NDIM, MODE_PLAIN>(maps, p, grid, s);
-    case MODE_SNAP_F32: return launch_one<R, NDIM, MODE_SNAP_F32>(maps, p, grid, s);
-    case MODE_SNAP_BF16: return launch_one<R, NDIM, MODE_SNAP_BF16>(maps, p, grid, s);
-    case MODE_SNAP_F16: return launch_one<R, NDIM, MODE_SNAP_F16>(maps, p, grid, s);
-    case MODE_GRAD_F32: return launch_one<R, NDIM, MODE_GRAD_F32>(maps, p, grid, s);
-    case MODE_GRAD_BF16: return launch_one<R, NDIM, MODE_GRAD_BF16>(maps, p, grid, s);
-    case MODE_GRAD_F16: return launch_one<R, NDIM, MODE_GRAD_F16>(maps, p, grid, s);
-    case MODE_BORN_SRC: return launch_one<R, NDIM, MODE_BORN_SRC>(maps, p, grid, s);
-    case MODE_SRC: return launch_one<R, NDIM, MODE_SRC>(maps, p, grid, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template <int R, int NDIM>
-static int smem_modes(int mode) {
-  switch (mode) {
-    case MODE_PLAIN: return StepLayout<R, NDIM, MODE_PLAIN>::SMEM;
-    case MODE_SNAP_F32: return StepLayout<R, NDIM, MODE_SNAP_F32>::SMEM;
-    case MODE_SNAP_BF16: return StepLayout<R, NDIM, MODE_SNAP_BF16>::SMEM;
-    case MODE_SNAP_F16: return StepLayout<R, NDIM, MODE_SNAP_F16>::SMEM;
-    case MODE_GRAD_F32: return StepLayout<R, NDIM, MODE_GRAD_F32>::SMEM;
-    case MODE_GRAD_BF16: return StepLayout<R, NDIM, MODE_GRAD_BF16>::SMEM;
-    case MODE_GRAD_F16: return StepLayout<R, NDIM, MODE_GRAD_F16>::SMEM;
-    case MODE_BORN_SRC: return StepLayout<R, NDIM, MODE_BORN_SRC>::SMEM;
-    case MODE_SRC: return StepLayout<R, NDIM, MODE_SRC>::SMEM;
-    default: return -1;
-  }
-}
-
 }  // namespace wave
-
-// Defines the per-radius entry points used by step_dispatch.cu.
-#define WAVE_DEFINE_STEP_RADIUS(RR)                                                                      \
-  namespace wave {                                                                                      \
-  cudaError_t launch_step_r##RR(int ndim, int mode, const StepMaps& maps, const StepParams& p, dim3 grid, \
-                                cudaStream_t s) {                                                       \
-    return ndim == 3 ? launch_modes<RR, 3>(mode, maps, p, grid, s) : launch_modes<RR, 2>(mode, maps, p, grid, s); \
-  }                                                                                                     \
-  int step_smem_r##RR(int ndim, int mode) { return ndim == 3 ? smem_modes<RR, 3>(mode) : smem_modes<RR, 2>(mode); } \
-  }

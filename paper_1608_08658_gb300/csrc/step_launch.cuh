@@ -1,0 +1,73 @@
+// Host-side launch helpers of the stencil step (per radius, dimension and
+// epilogue mode); included by the per-radius translation units.
+#pragma once
+
+#include <atomic>
+
+#include "step_kernel.cuh"
+
+namespace wave {
+
+// Host launcher for one radius; instantiated once per step_r<R>.cu.
+template <int R, int NDIM, int MODE>
+static cudaError_t launch_one(const StepMaps& maps, const StepParams& p, dim3 grid, cudaStream_t stream) {
+  using T = StepTraits<R, NDIM>;
+  using L = StepLayout<R, NDIM, MODE>;
+  // the dynamic shared-memory limit is a per-device function attribute
+  static std::atomic<unsigned long long> configured{0};
+  int device = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (device & 63);
+  if (!(configured.load(std::memory_order_acquire) & bit)) {
+    e = cudaFuncSetAttribute(dev::step_kernel<R, NDIM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+    if (e != cudaSuccess) return e;
+    configured.fetch_or(bit, std::memory_order_acq_rel);
+  }
+  dev::step_kernel<R, NDIM, MODE><<<grid, T::NTHREADS, L::SMEM, stream>>>(maps.u, maps.p, maps.cm, maps.g, maps.s, p);
+  return cudaGetLastError();
+}
+
+template <int R, int NDIM>
+static cudaError_t launch_modes(int mode, const StepMaps& maps, const StepParams& p, dim3 grid, cudaStream_t s) {
+  switch (mode) {
+    case MODE_PLAIN: return launch_one<R, NDIM, MODE_PLAIN>(maps, p, grid, s);
+    case MODE_SNAP_F32: return launch_one<R, NDIM, MODE_SNAP_F32>(maps, p, grid, s);
+    case MODE_SNAP_BF16: return launch_one<R, NDIM, MODE_SNAP_BF16>(maps, p, grid, s);
+    case MODE_SNAP_F16: return launch_one<R, NDIM, MODE_SNAP_F16>(maps, p, grid, s);
+    case MODE_GRAD_F32: return launch_one<R, NDIM, MODE_GRAD_F32>(maps, p, grid, s);
+    case MODE_GRAD_BF16: return launch_one<R, NDIM, MODE_GRAD_BF16>(maps, p, grid, s);
+    case MODE_GRAD_F16: return launch_one<R, NDIM, MODE_GRAD_F16>(maps, p, grid, s);
+    case MODE_BORN_SRC: return launch_one<R, NDIM, MODE_BORN_SRC>(maps, p, grid, s);
+    case MODE_SRC: return launch_one<R, NDIM, MODE_SRC>(maps, p, grid, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int R, int NDIM>
+static int smem_modes(int mode) {
+  switch (mode) {
+    case MODE_PLAIN: return StepLayout<R, NDIM, MODE_PLAIN>::SMEM;
+    case MODE_SNAP_F32: return StepLayout<R, NDIM, MODE_SNAP_F32>::SMEM;
+    case MODE_SNAP_BF16: return StepLayout<R, NDIM, MODE_SNAP_BF16>::SMEM;
+    case MODE_SNAP_F16: return StepLayout<R, NDIM, MODE_SNAP_F16>::SMEM;
+    case MODE_GRAD_F32: return StepLayout<R, NDIM, MODE_GRAD_F32>::SMEM;
+    case MODE_GRAD_BF16: return StepLayout<R, NDIM, MODE_GRAD_BF16>::SMEM;
+    case MODE_GRAD_F16: return StepLayout<R, NDIM, MODE_GRAD_F16>::SMEM;
+    case MODE_BORN_SRC: return StepLayout<R, NDIM, MODE_BORN_SRC>::SMEM;
+    case MODE_SRC: return StepLayout<R, NDIM, MODE_SRC>::SMEM;
+    default: return -1;
+  }
+}
+
+}  // namespace wave
+
+// Defines the per-radius entry points used by step_dispatch.cu.
+#define WAVE_DEFINE_STEP_RADIUS(RR)                                                                      \
+  namespace wave {                                                                                      \
+  cudaError_t launch_step_r##RR(int ndim, int mode, const StepMaps& maps, const StepParams& p, dim3 grid, \
+                                cudaStream_t s) {                                                       \
+    return ndim == 3 ? launch_modes<RR, 3>(mode, maps, p, grid, s) : launch_modes<RR, 2>(mode, maps, p, grid, s); \
+  }                                                                                                     \
+  int step_smem_r##RR(int ndim, int mode) { return ndim == 3 ? smem_modes<RR, 3>(mode) : smem_modes<RR, 2>(mode); } \
+  }

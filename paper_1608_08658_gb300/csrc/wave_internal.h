@@ -60,6 +60,11 @@ constexpr int kSlabY = 2;
 #define WAVE_BY14_MIN_R 8
 #endif
 
+// Shared memory of one SM and the part the driver keeps per resident CTA.
+constexpr int kSmemPerSm = 228 * 1024;
+constexpr int kSmemReservedPerCta = 1024;
+constexpr int kSmemTwoCtas = kSmemPerSm / 2 - kSmemReservedPerCta;  // per CTA at two CTAs per SM
+
 template <int R, int NDIM>
 struct StepTraits {
   static constexpr int BX = 64;                   // x outputs per CTA (16 threads x 4)
@@ -69,46 +74,66 @@ struct StepTraits {
   static constexpr int BY = (NDIM == 3 && R >= WAVE_BY14_MIN_R) ? 14 : 16;
   static constexpr int HX = (R <= 4) ? 4 : 8;     // x halo, rounded to 16 bytes for TMA
   static constexpr int RZ = (NDIM == 3) ? R : 0;  // halo along the streamed axis
-  static constexpr int PF = (NDIM == 3) ? 2 : 0;  // extra planes prefetched ahead
-  // Lead-plane design for radius 7-8: the register queue is fed from a
-  // small ring of interior boxes of plane z+R, and the halo box of the centre
-  // plane is loaded again (from L2) with the per-point tiles, so the shared
-  // ring holds only the prefetch depth instead of R+1+PF halo planes.
-  static constexpr bool LEAD = (NDIM == 3) && (R >= WAVE_LEAD_MIN_R);
   static constexpr int UW = BX + 2 * HX;          // smem row length of a halo box (floats)
   static constexpr int UH = BY + 2 * R;           // rows of a halo box
   static constexpr int U_BYTES = UW * UH * 4;                // bytes of one halo box
   static constexpr int U_STRIDE = (U_BYTES + 127) / 128 * 128;  // halo box spacing (128-byte aligned)
   static constexpr int T_ELEMS = BX * BY;
-  // queue-feed ring: halo planes (classic) or interior boxes (lead)
-  static constexpr int NSU = LEAD ? PF + 1 : RZ + 1 + PF;
-  static constexpr int Q_BYTES = LEAD ? T_ELEMS * 4 : U_BYTES;
-  static constexpr int Q_STRIDE = LEAD ? T_ELEMS * 4 : U_STRIDE;
   // per-plane ring: per-point tiles (+ the centre halo box in the lead design)
   static constexpr int NSP = (NDIM == 3) ? 3 : 1;
   static constexpr int NCW = BY / 2;              // consumer warps
   static constexpr int NTHREADS = (NCW + 1) * 32; // + one producer warp
 };
 
-// Per-point tiles loaded with each plane (bytes), by mode.
+// Shared-memory layout, prefetch depth and occupancy of one (R, NDIM, MODE).
 template <int R, int NDIM, int MODE>
 struct StepLayout {
   using T = StepTraits<R, NDIM>;
   static constexpr int SNAP_ELEM = mode_snap_fmt(MODE) == 0 ? 4 : 2;
+  // per-point tiles loaded with each plane: previous level, cm, and g (the
+  // gradient, dm or S) and the snapshot where the mode needs them
+  static constexpr int TILE_BYTES = mode_is_grad(MODE) ? (3 * T::T_ELEMS * 4 + T::T_ELEMS * SNAP_ELEM)
+                                                       : (mode_loads_g(MODE) ? 3 : 2) * T::T_ELEMS * 4;
+  // 2*(NSU+NSP) mbarriers + an abort flag, padded to 128 bytes
+  static constexpr int bar_bytes(int nsu) { return ((16 * (nsu + T::NSP) + 16 + 127) / 128) * 128; }
+  // Classic design: the queue-feed ring holds halo planes z .. z+R+pf, and
+  // the per-point ring the tiles.
+  static constexpr int classic_smem(int pf) {
+    return bar_bytes(T::RZ + 1 + pf) + (T::RZ + 1 + pf) * T::U_STRIDE + T::NSP * TILE_BYTES + 128;
+  }
+  // Lead-plane design: the register queue is fed from a small ring of
+  // interior boxes of plane z+R, and the halo box of the centre plane is
+  // loaded again (from L2) with the per-point tiles, so the shared ring holds
+  // only the prefetch depth instead of R+1+PF halo planes.  Used from radius 7
+  // on, and wherever the classic design would not fit two CTAs per SM.
+  static constexpr bool LEAD = (NDIM == 3) && (R >= WAVE_LEAD_MIN_R || classic_smem(2) > kSmemTwoCtas);
+  // Deep variant (classic design, radius <= 5, not the imaging condition):
+  // two CTAs per SM with a 4-plane prefetch and planes taken in pairs (half
+  // the register-queue moves), which the 96 registers per thread at two CTAs
+  // allow.  The imaging steps are HBM-bound and keep the 2-plane prefetch.
+  static constexpr bool DEEP =
+      NDIM == 3 && !LEAD && R <= 5 && !mode_is_grad(MODE) && classic_smem(4) <= kSmemTwoCtas;
+  static constexpr int PF = NDIM == 3 ? (DEEP ? 4 : 2) : 0;  // planes prefetched ahead
+  static constexpr int NSU = LEAD ? PF + 1 : T::RZ + 1 + PF;  // queue-feed ring stages
+  static constexpr int Q_BYTES = LEAD ? T::T_ELEMS * 4 : T::U_BYTES;
+  static constexpr int Q_STRIDE = LEAD ? T::T_ELEMS * 4 : T::U_STRIDE;
+  static constexpr int QU = DEEP ? 2 : 1;  // output planes per register-queue move
+  // resident CTAs per SM asked of the register allocator (registers per
+  // thread follow the warps per SM sub-partition: 3 CTAs of 9 warps leave 72,
+  // 2 of 9 leave 96, 2 of 8 leave 128)
+  static constexpr int MIN_BLOCKS = (NDIM == 2 && R <= 4 && !mode_is_grad(MODE)) ? 3 : 2;
+
   static constexpr int HALO_OFF = 0;                        // lead design: centre halo box
-  static constexpr int PREV_OFF = T::LEAD ? T::U_STRIDE : 0;
+  static constexpr int PREV_OFF = LEAD ? T::U_STRIDE : 0;
   static constexpr int CM_OFF = PREV_OFF + T::T_ELEMS * 4;
   static constexpr int G_OFF = CM_OFF + T::T_ELEMS * 4;
   static constexpr int S_OFF = G_OFF + T::T_ELEMS * 4;
-  static constexpr int TILE_BYTES = mode_is_grad(MODE) ? (3 * T::T_ELEMS * 4 + T::T_ELEMS * SNAP_ELEM)
-                                                       : (mode_loads_g(MODE) ? 3 : 2) * T::T_ELEMS * 4;
-  static constexpr int P_TX = (T::LEAD ? T::U_BYTES : 0) + TILE_BYTES;  // bytes landing per plane stage
-  static constexpr int P_BYTES = PREV_OFF + TILE_BYTES;                   // stage spacing
+  static constexpr int P_TX = (LEAD ? T::U_BYTES : 0) + TILE_BYTES;  // bytes landing per plane stage
+  static constexpr int P_BYTES = PREV_OFF + TILE_BYTES;                // stage spacing
   static_assert(P_BYTES % 128 == 0, "per-point stage must keep 128-byte alignment");
-  // 2*(NSU+NSP) mbarriers + an abort flag, padded to 128 bytes
-  static constexpr int BAR_BYTES = ((16 * (T::NSU + T::NSP) + 16 + 127) / 128) * 128;
+  static constexpr int BAR_BYTES = bar_bytes(NSU);
   static constexpr int U_OFF = BAR_BYTES;
-  static constexpr int PST_OFF = U_OFF + T::NSU * T::Q_STRIDE;
+  static constexpr int PST_OFF = U_OFF + NSU * Q_STRIDE;
   static constexpr int SMEM = PST_OFF + T::NSP * P_BYTES + 128;  // + runtime 128-byte alignment
 };
 
@@ -153,9 +178,8 @@ struct StepMaps {
 
 cudaError_t launch_step(int R, int ndim, int mode, const StepMaps& maps, const StepParams& p,
                         dim3 grid, cudaStream_t stream);
-// NOTE: step_by() must agree with StepTraits<R, NDIM>::BY.
+// Tile geometry of StepTraits<R, NDIM> for the host (maps and grid).
 int step_smem_bytes(int R, int ndim, int mode);
-int step_threads();
 int step_bx();
 int step_by(int R, int ndim);
 int step_hx(int R);
