@@ -124,7 +124,7 @@ __global__ void inject_coef_kernel(InjectSet is, GridDims g, const float* __rest
   if (g.NZ > 1) eta += dev::sponge_term(z, g.NZ, g.nblz, emz);
   const float c = cm[cell];
   const float kk = eta * c * half_inv_dt;
-  const float inv = eta == 0.f ? 1.f : __frcp_rn(1.f + kk);
+  const float inv = eta == 0.f ? 1.f : __fdividef(1.f, 1.f + kk);  // as in the step kernel
   is.coef[k] = c * inv;
 }
 

@@ -46,10 +46,14 @@ __device__ __forceinline__ float get(const float4& v, int i) {
   return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
 }
 
+// 1/(1+k) and 1-k of the damped update.  1+k >= 1 is a moderate number, for
+// which the fast division intrinsic is within 2 ulp; the correctly rounded
+// reciprocal costs a longer instruction sequence at every sponge point.  The
+// source-injection coefficient uses the same expression.
 __device__ __forceinline__ float damp_inv(float eta, float cm, float half_inv_dt, float& one_minus_k) {
   const float k = eta * cm * half_inv_dt;
   one_minus_k = 1.f - k;
-  return eta == 0.f ? 1.f : __frcp_rn(1.f + k);
+  return eta == 0.f ? 1.f : __fdividef(1.f, 1.f + k);
 }
 
 template <int FMT>
@@ -94,7 +98,7 @@ struct IntC {
   static constexpr int value = V;
 };
 
-template <int R, int NDIM, int MODE>
+template <int R, int NDIM, int MODE, bool ISO>
 __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepLayout<R, NDIM, MODE>::MIN_BLOCKS))
     step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
                 const __grid_constant__ CUtensorMap tm_cm, const __grid_constant__ CUtensorMap tm_g,
@@ -217,21 +221,23 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepLayout<R, 
   // all terms are >= 0: the column is undamped iff the largest is zero
   const float exy_max = fmaxf(fmaxf(exy[0], exy[1]), fmaxf(exy[2], exy[3]));
 
-  // Coefficients as packed pairs (loop invariant) up to radius 6; above, the
-  // 6R pairs would cost too many registers, so the multiply takes the scalar
-  // coefficient from the parameter bank and only the sums stay packed.
-  constexpr bool PCOEF = R <= 6;
+  // Coefficients as packed pairs (loop invariant).  With different spacings
+  // per axis there are 3R of them, which up to radius 6 fit in registers;
+  // above, the multiply takes the scalar coefficient from the parameter bank
+  // and only the sums stay packed.  With equal spacing on every axis (ISO) one
+  // coefficient per offset serves all axes: R pairs, kept in registers.
+  constexpr bool PCOEF = ISO || R <= 6;
   constexpr int NPC = PCOEF ? R : 1;
   const float2 c0v = make_float2(p.c0, p.c0);
-  float2 cxv[NPC], cyv[NPC], czv[PCOEF && RZ > 0 ? RZ : 1];
+  float2 cxv[NPC], cyv[ISO ? 1 : NPC], czv[!ISO && PCOEF && RZ > 0 ? RZ : 1];
 #pragma unroll
-  for (int k = 0; k < NPC; ++k) {
-    cxv[k] = make_float2(p.cx[k], p.cx[k]);
-    cyv[k] = make_float2(p.cy[k], p.cy[k]);
-  }
+  for (int k = 0; k < NPC; ++k) cxv[k] = make_float2(p.cx[k], p.cx[k]);
 #pragma unroll
-  for (int k = 0; k < (PCOEF ? RZ : 0); ++k) czv[k] = make_float2(p.cz[k], p.cz[k]);
-  // acc += c_{axis,k} * (a + b) on a packed pair (axis 0 = x, 1 = axis 1, 2 = axis 2)
+  for (int k = 0; k < (ISO ? 0 : NPC); ++k) cyv[k] = make_float2(p.cy[k], p.cy[k]);
+#pragma unroll
+  for (int k = 0; k < (!ISO && PCOEF ? RZ : 0); ++k) czv[k] = make_float2(p.cz[k], p.cz[k]);
+  // acc += c_{axis,k} * (a + b) on a packed pair (axis 0 = x, 1 = axis 1, 2 = axis 2);
+  // anisotropic spacing only
   auto tap2 = [&](float2& acc, int axis, int k, const float2& a, const float2& b) {
     const float2 sum = __fadd2_rn(a, b);
     if constexpr (PCOEF) {
@@ -311,19 +317,46 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepLayout<R, 
     // Laplacian on two packed pairs (points 0,1 and 2,3 of the quad)
     float2 la = __fmul2_rn(c0v, make_float2(c.x, c.y));
     float2 lb = __fmul2_rn(c0v, make_float2(c.z, c.w));
+    if constexpr (ISO) {
+      // one coefficient per offset k: the axis-2 and axis-1 neighbour pairs
+      // at distance k are summed before a single multiply
 #pragma unroll
-    for (int k = 1; k <= RZ; ++k) {
-      const float4 a = q[O + RZ - k];
-      const float4 b = q[O + RZ + k];
-      tap2(la, 2, k - 1, make_float2(a.x, a.y), make_float2(b.x, b.y));
-      tap2(lb, 2, k - 1, make_float2(a.z, a.w), make_float2(b.z, b.w));
-    }
+      for (int k = 1; k <= R; ++k) {
+        const float4 ya = lds4(Uc - k * T::UW);
+        const float4 yb = lds4(Uc + k * T::UW);
+        float2 sa = __fadd2_rn(make_float2(ya.x, ya.y), make_float2(yb.x, yb.y));
+        float2 sb = __fadd2_rn(make_float2(ya.z, ya.w), make_float2(yb.z, yb.w));
+        if constexpr (RZ > 0) {
+          const float4 za = q[O + RZ - k];
+          const float4 zb = q[O + RZ + k];
+          sa = __fadd2_rn(sa, __fadd2_rn(make_float2(za.x, za.y), make_float2(zb.x, zb.y)));
+          sb = __fadd2_rn(sb, __fadd2_rn(make_float2(za.z, za.w), make_float2(zb.z, zb.w)));
+        }
+        if constexpr (PCOEF) {
+          la = __ffma2_rn(cxv[k - 1], sa, la);
+          lb = __ffma2_rn(cxv[k - 1], sb, lb);
+        } else {
+          la.x = fmaf(p.cx[k - 1], sa.x, la.x);
+          la.y = fmaf(p.cx[k - 1], sa.y, la.y);
+          lb.x = fmaf(p.cx[k - 1], sb.x, lb.x);
+          lb.y = fmaf(p.cx[k - 1], sb.y, lb.y);
+        }
+      }
+    } else {
 #pragma unroll
-    for (int k = 1; k <= R; ++k) {
-      const float4 a = lds4(Uc - k * T::UW);
-      const float4 b = lds4(Uc + k * T::UW);
-      tap2(la, 1, k - 1, make_float2(a.x, a.y), make_float2(b.x, b.y));
-      tap2(lb, 1, k - 1, make_float2(a.z, a.w), make_float2(b.z, b.w));
+      for (int k = 1; k <= RZ; ++k) {
+        const float4 a = q[O + RZ - k];
+        const float4 b = q[O + RZ + k];
+        tap2(la, 2, k - 1, make_float2(a.x, a.y), make_float2(b.x, b.y));
+        tap2(lb, 2, k - 1, make_float2(a.z, a.w), make_float2(b.z, b.w));
+      }
+#pragma unroll
+      for (int k = 1; k <= R; ++k) {
+        const float4 a = lds4(Uc - k * T::UW);
+        const float4 b = lds4(Uc + k * T::UW);
+        tap2(la, 1, k - 1, make_float2(a.x, a.y), make_float2(b.x, b.y));
+        tap2(lb, 1, k - 1, make_float2(a.z, a.w), make_float2(b.z, b.w));
+      }
     }
     {
       constexpr int NH = T::HX / 4;  // halo quads per side
@@ -379,11 +412,15 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepLayout<R, 
     const float ez = NDIM == 3 ? sponge_term(gz, p.NZ, p.nblz, p.emz) : 0.f;
     float4 out;
     if (exy_max + ez == 0.f) {
-      // undamped: new = 2 cur - prev + cm L (the damped formula at k = 0)
-      out.x = fmaf(cm.x, lap.x, fmaf(-1.f, prev.x, 2.f * c.x));
-      out.y = fmaf(cm.y, lap.y, fmaf(-1.f, prev.y, 2.f * c.y));
-      out.z = fmaf(cm.z, lap.z, fmaf(-1.f, prev.z, 2.f * c.z));
-      out.w = fmaf(cm.w, lap.w, fmaf(-1.f, prev.w, 2.f * c.w));
+      // undamped: new = 2 cur - prev + cm L (the damped formula at k = 0), on
+      // packed pairs
+      const float2 m1 = make_float2(-1.f, -1.f);
+      const float2 ca = make_float2(c.x, c.y), cb = make_float2(c.z, c.w);
+      const float2 oa = __ffma2_rn(make_float2(cm.x, cm.y), la,
+                                   __ffma2_rn(m1, make_float2(prev.x, prev.y), __fadd2_rn(ca, ca)));
+      const float2 ob = __ffma2_rn(make_float2(cm.z, cm.w), lb,
+                                   __ffma2_rn(m1, make_float2(prev.z, prev.w), __fadd2_rn(cb, cb)));
+      out = make_float4(oa.x, oa.y, ob.x, ob.y);
     } else {
       float omk;
       float inv = damp_inv(exy[0] + ez, cm.x, p.half_inv_dt, omk);

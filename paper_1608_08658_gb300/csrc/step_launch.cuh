@@ -9,8 +9,8 @@
 namespace wave {
 
 // Host launcher for one radius; instantiated once per step_r<R>.cu.
-template <int R, int NDIM, int MODE>
-static cudaError_t launch_one(const StepMaps& maps, const StepParams& p, dim3 grid, cudaStream_t stream) {
+template <int R, int NDIM, int MODE, bool ISO>
+static cudaError_t launch_iso(const StepMaps& maps, const StepParams& p, dim3 grid, cudaStream_t stream) {
   using T = StepTraits<R, NDIM>;
   using L = StepLayout<R, NDIM, MODE>;
   // the dynamic shared-memory limit is a per-device function attribute
@@ -20,12 +20,23 @@ static cudaError_t launch_one(const StepMaps& maps, const StepParams& p, dim3 gr
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (device & 63);
   if (!(configured.load(std::memory_order_acquire) & bit)) {
-    e = cudaFuncSetAttribute(dev::step_kernel<R, NDIM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+    e = cudaFuncSetAttribute(dev::step_kernel<R, NDIM, MODE, ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
     if (e != cudaSuccess) return e;
     configured.fetch_or(bit, std::memory_order_acq_rel);
   }
-  dev::step_kernel<R, NDIM, MODE><<<grid, T::NTHREADS, L::SMEM, stream>>>(maps.u, maps.p, maps.cm, maps.g, maps.s, p);
+  dev::step_kernel<R, NDIM, MODE, ISO><<<grid, T::NTHREADS, L::SMEM, stream>>>(maps.u, maps.p, maps.cm, maps.g, maps.s, p);
   return cudaGetLastError();
+}
+
+// Equal spacing on every axis selects, at radius 8, the kernel with one
+// coefficient per offset (measured faster there; slower at radius 5-7 and
+// equal below, where the general kernel is kept).
+template <int R, int NDIM, int MODE>
+static cudaError_t launch_one(const StepMaps& maps, const StepParams& p, dim3 grid, cudaStream_t stream) {
+  if constexpr (R == 8) {
+    if (p.iso) return launch_iso<R, NDIM, MODE, true>(maps, p, grid, stream);
+  }
+  return launch_iso<R, NDIM, MODE, false>(maps, p, grid, stream);
 }
 
 template <int R, int NDIM>

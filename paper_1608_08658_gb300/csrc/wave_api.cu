@@ -388,6 +388,9 @@ int prepare(wave_context* ctx, const wave_geometry* geom, float dt, int nt, int 
     sp.cy[j - 1] = static_cast<float>(w * inv_h2[1]);
     sp.cz[j - 1] = static_cast<float>(w * inv_h2[2]);
   }
+  sp.iso = 1;
+  for (int j = 0; j < P->R; ++j)
+    if (sp.cx[j] != sp.cy[j] || (nd == 3 && sp.cy[j] != sp.cz[j])) sp.iso = 0;
   sp.nblx = g.nblx;
   sp.nbly = g.nbly;
   sp.nblz = g.nblz;

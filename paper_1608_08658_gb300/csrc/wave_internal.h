@@ -151,6 +151,7 @@ struct StepParams {
   // stencil coefficients (1/h^2 folded in): lap = c0*u + sum_j c{x,y,z}[j-1]*(u[-j]+u[+j])
   float c0;
   float cx[8], cy[8], cz[8];
+  int iso;                 // 1 when cx == cy (== cz): equal spacing on every axis
   // sponge: eta = sum_axis eta_max_axis * (delta/nbl)^2 ; nbl per kernel axis (0 on a missing axis)
   int nblx, nbly, nblz;
   float emx, emy, emz;     // eta_max per axis divided by nbl^2 (1/ms)

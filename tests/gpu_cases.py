@@ -31,10 +31,12 @@ def config1():
     return og, m, dt, nt, so, src, q, rec
 
 
-def small3d(so, shape=(83, 21, 40), nbl=5, nt=60, seed=0, nsrc=2, nrec=25):
+def small3d(so, shape=(83, 21, 40), nbl=5, nt=60, seed=0, nsrc=2, nrec=25, spacing=(10.0, 12.0, 9.0)):
     """Small 3D case with ragged tiles and several z chunks; sources and
-    receivers off-grid, on nodes, on tile edges and on the last node."""
-    og = oracle.model.Geometry(shape=shape, spacing=(10.0, 12.0, 9.0), origin=(3.0, -7.0, 0.0), nbl=nbl,
+    receivers off-grid, on nodes, on tile edges and on the last node.  The
+    default spacing differs per axis; equal spacing selects the kernel that
+    shares one coefficient per offset between the axes."""
+    og = oracle.model.Geometry(shape=shape, spacing=spacing, origin=(3.0, -7.0, 0.0), nbl=nbl,
                                sponge_vref=2.5)
     r = inputs.rng(seed)
     v = 1.5 + 1.0 * r.uniform(size=og.phys_array_shape)
@@ -46,8 +48,9 @@ def small3d(so, shape=(83, 21, 40), nbl=5, nt=60, seed=0, nsrc=2, nrec=25):
     rec = lo + r.uniform(size=(nrec, 3)) * (hi - lo)
     rec[0] = lo                                   # first physical node
     rec[1] = hi                                   # last physical node
-    rec[2] = lo + np.array([(64 - nbl) * 10.0, (16 - nbl) * 12.0, 4 * 9.0])   # tile corner node
-    rec[3] = lo + np.array([(63.5 - nbl) * 10.0, 3.25 * 12.0, 17.7 * 9.0])   # straddles an x tile edge
+    hx, hy, hz = spacing
+    rec[2] = lo + np.array([(64 - nbl) * hx, (16 - nbl) * hy, 4 * hz])   # tile corner node
+    rec[3] = lo + np.array([(63.5 - nbl) * hx, 3.25 * hy, 17.7 * hz])   # straddles an x tile edge
     rec = rec.astype(np.float32)
     q = (r.standard_normal((nt, nsrc)) * 1e2).astype(np.float32)
     return og, m, dt, nt, so, src, q, rec

@@ -26,10 +26,11 @@ def _dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-@pytest.mark.parametrize("case", ["3d8", "2d4", "3d16"])
+@pytest.mark.parametrize("case", ["3d8", "2d4", "3d12", "3d16", "3d8iso", "3d16iso"])
 def test_born_matches_oracle(ctx, case):
-    so = {"3d8": 8, "2d4": 4, "3d16": 16}[case]
-    og, m, dt, nt, so, src, q, rec = small3d(so) if case.startswith("3d") else small2d(so)
+    so = int(case[2:].replace("iso", ""))
+    h = (10.0, 10.0, 10.0) if case.endswith("iso") else (10.0, 12.0, 9.0)
+    og, m, dt, nt, so, src, q, rec = small3d(so, spacing=h) if case.startswith("3d") else small2d(so)
     _, geom = geometries(og)
     rng = np.random.default_rng(41)
     dm = (0.05 * m * rng.uniform(-1, 1, size=m.shape)).astype(np.float32)

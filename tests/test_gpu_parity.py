@@ -40,15 +40,16 @@ def test_forward_2d_101x101_order4(ctx):
     assert err <= 1e-4
 
 
+@pytest.mark.parametrize("iso", [False, True])
 @pytest.mark.parametrize("so", [2, 4, 6, 8, 10, 12, 14, 16])
-def test_forward_3d_all_orders(ctx, so):
-    og, m, dt, nt, so, src, q, rec = small3d(so)
+def test_forward_3d_all_orders(ctx, so, iso):
+    og, m, dt, nt, so, src, q, rec = small3d(so, spacing=(10.0, 10.0, 10.0) if iso else (10.0, 12.0, 9.0))
     _, geom = geometries(og)
     d, fp, fl = wave.wave_forward(ctx, geom, _dev(m), src, _dev(q), rec, dt, nt, so, return_final=True)
     ref = oracle.wave.forward(og, m, dt, nt, so, q, src, rec)
     e_d = rel_l2(d.cpu().numpy(), ref.d)
     e_u = np.abs(fl.cpu().numpy() - ref.u_last).max() / np.abs(ref.u_last).max()
-    print("3D so%d: rel-L2 receivers %.3e, max field err %.3e" % (so, e_d, e_u))
+    print("3D so%d%s: rel-L2 receivers %.3e, max field err %.3e" % (so, " (equal spacing)" if iso else "", e_d, e_u))
     assert e_d <= 1e-4 and e_u <= 1e-4
 
 
@@ -61,9 +62,11 @@ def test_forward_2d_all_orders(ctx, so):
     assert rel_l2(d, ref) <= 1e-4
 
 
-@pytest.mark.parametrize("so,ndim", [(2, 3), (8, 3), (16, 3), (4, 2), (14, 2)])
-def test_single_step_from_random_state(ctx, so, ndim):
-    og, m, dt, _, so, src, _, rec = small3d(so, nt=2) if ndim == 3 else small2d(so, nt=2)
+@pytest.mark.parametrize("so,ndim,iso", [(2, 3, False), (8, 3, False), (16, 3, False), (8, 3, True), (14, 3, True),
+                                         (16, 3, True), (4, 2, False), (14, 2, False)])
+def test_single_step_from_random_state(ctx, so, ndim, iso):
+    h = (10.0, 10.0, 10.0) if iso else (10.0, 12.0, 9.0)
+    og, m, dt, _, so, src, _, rec = small3d(so, nt=2, spacing=h) if ndim == 3 else small2d(so, nt=2)
     _, geom = geometries(og)
     r = np.random.default_rng(77)
     u0 = r.standard_normal(og.array_shape).astype(np.float32)
@@ -98,10 +101,11 @@ def test_adjoint_and_dot_product(ctx, case):
     assert abs(lhs - rhs) <= 1e-4 * max(abs(lhs), abs(rhs))
 
 
-@pytest.mark.parametrize("case", ["3d8", "2d4", "3d16"])
+@pytest.mark.parametrize("case", ["3d8", "2d4", "3d10", "3d12", "3d16", "3d8iso", "3d14iso", "3d16iso"])
 def test_gradient_full_fp32(ctx, case):
-    so = {"3d8": 8, "2d4": 4, "3d16": 16}[case]
-    og, m, dt, nt, so, src, q, rec = small3d(so) if case.startswith("3d") else small2d(so)
+    so = int(case[2:].replace("iso", ""))
+    h = (12.5, 12.5, 12.5) if case.endswith("iso") else (10.0, 12.0, 9.0)
+    og, m, dt, nt, so, src, q, rec = small3d(so, spacing=h) if case.startswith("3d") else small2d(so)
     _, geom = geometries(og)
     r = np.random.default_rng(9)
     d_obs = (oracle.wave.forward(og, m * 1.02, dt, nt, so, q, src, rec).d).astype(np.float32)
@@ -113,6 +117,18 @@ def test_gradient_full_fp32(ctx, case):
     print("%s gradient: rel-L2 %.3e, objective rel %.3e" % (case, e_g, e_phi))
     assert e_g <= 5e-4 and e_phi <= 1e-4
     del r
+
+
+@pytest.mark.parametrize("so", [10, 12])
+def test_gradient_fp16_snapshots_high_order(ctx, so):
+    og, m, dt, nt, so, src, q, rec = small3d(so)
+    _, geom = geometries(og)
+    d_obs = (oracle.wave.forward(og, m * 1.02, dt, nt, so, q, src, rec).d).astype(np.float32)
+    g, _ = wave.wave_gradient(ctx, geom, _dev(m), src, _dev(q), rec, _dev(d_obs), dt, nt, so, snap_mode="full_fp16")
+    g_ref, _ = oracle.wave.gradient(og, m, dt, nt, so, q, src, rec, d_obs)
+    e_g = rel_l2(g.cpu().numpy(), g_ref)
+    print("3D so%d gradient, FP16 snapshots: rel-L2 %.3e" % (so, e_g))
+    assert e_g <= 5e-4
 
 
 def test_gradient_storage_modes(ctx):
