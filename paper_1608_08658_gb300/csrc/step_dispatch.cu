@@ -6,7 +6,7 @@ namespace wave {
 #define WAVE_DECLARE_RADIUS(RR)                                                                          \
   cudaError_t launch_step_r##RR(int ndim, int mode, const StepMaps& maps, const StepParams& p, dim3 grid, \
                                 cudaStream_t s);                                                        \
-  int step_smem_r##RR(int ndim, int mode);
+  int step_smem_r##RR(int ndim, int mode, bool iso);
 WAVE_DECLARE_RADIUS(1)
 WAVE_DECLARE_RADIUS(2)
 WAVE_DECLARE_RADIUS(3)
@@ -31,23 +31,24 @@ cudaError_t launch_step(int R, int ndim, int mode, const StepMaps& maps, const S
   }
 }
 
-int step_smem_bytes(int R, int ndim, int mode) {
+int step_smem_bytes(int R, int ndim, int mode, bool iso) {
   switch (R) {
-    case 1: return step_smem_r1(ndim, mode);
-    case 2: return step_smem_r2(ndim, mode);
-    case 3: return step_smem_r3(ndim, mode);
-    case 4: return step_smem_r4(ndim, mode);
-    case 5: return step_smem_r5(ndim, mode);
-    case 6: return step_smem_r6(ndim, mode);
-    case 7: return step_smem_r7(ndim, mode);
-    case 8: return step_smem_r8(ndim, mode);
+    case 1: return step_smem_r1(ndim, mode, iso);
+    case 2: return step_smem_r2(ndim, mode, iso);
+    case 3: return step_smem_r3(ndim, mode, iso);
+    case 4: return step_smem_r4(ndim, mode, iso);
+    case 5: return step_smem_r5(ndim, mode, iso);
+    case 6: return step_smem_r6(ndim, mode, iso);
+    case 7: return step_smem_r7(ndim, mode, iso);
+    case 8: return step_smem_r8(ndim, mode, iso);
     default: return -1;
   }
 }
 
 int step_bx() { return StepTraits<1, 3>::BX; }
-int step_by(int R, int ndim) {
+int step_by(int R, int ndim, bool iso) {
   if (ndim != 3) return StepTraits<1, 2>::BY;
+  if (iso_kernel(R, iso)) return R == 7 ? StepTraits<7, 3, true>::BY : StepTraits<8, 3, true>::BY;
   switch (R) {
     case 1: return StepTraits<1, 3>::BY;
     case 2: return StepTraits<2, 3>::BY;

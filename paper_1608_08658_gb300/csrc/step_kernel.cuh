@@ -99,12 +99,12 @@ struct IntC {
 };
 
 template <int R, int NDIM, int MODE, bool ISO>
-__global__ void __launch_bounds__(StepTraits<R, NDIM>::NTHREADS, (StepLayout<R, NDIM, MODE>::MIN_BLOCKS))
+__global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayout<R, NDIM, MODE, ISO>::MIN_BLOCKS))
     step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
                 const __grid_constant__ CUtensorMap tm_cm, const __grid_constant__ CUtensorMap tm_g,
                 const __grid_constant__ CUtensorMap tm_s, const StepParams p) {
-  using T = StepTraits<R, NDIM>;
-  using L = StepLayout<R, NDIM, MODE>;
+  using T = StepTraits<R, NDIM, ISO>;
+  using L = StepLayout<R, NDIM, MODE, ISO>;
   constexpr int RZ = T::RZ;
   constexpr int FMT = mode_snap_fmt(MODE);
 

@@ -11,8 +11,8 @@ namespace wave {
 // Host launcher for one radius; instantiated once per step_r<R>.cu.
 template <int R, int NDIM, int MODE, bool ISO>
 static cudaError_t launch_iso(const StepMaps& maps, const StepParams& p, dim3 grid, cudaStream_t stream) {
-  using T = StepTraits<R, NDIM>;
-  using L = StepLayout<R, NDIM, MODE>;
+  using T = StepTraits<R, NDIM, ISO>;
+  using L = StepLayout<R, NDIM, MODE, ISO>;
   // the dynamic shared-memory limit is a per-device function attribute
   static std::atomic<unsigned long long> configured{0};
   int device = 0;
@@ -28,12 +28,10 @@ static cudaError_t launch_iso(const StepMaps& maps, const StepParams& p, dim3 gr
   return cudaGetLastError();
 }
 
-// Equal spacing on every axis selects, at radius 8, the kernel with one
-// coefficient per offset (measured faster there; slower at radius 5-7 and
-// equal below, where the general kernel is kept).
+// p.iso selects the equal-spacing variant (instantiated from radius kIsoMinR)
 template <int R, int NDIM, int MODE>
 static cudaError_t launch_one(const StepMaps& maps, const StepParams& p, dim3 grid, cudaStream_t stream) {
-  if constexpr (R == 8) {
+  if constexpr (R >= kIsoMinR) {
     if (p.iso) return launch_iso<R, NDIM, MODE, true>(maps, p, grid, stream);
   }
   return launch_iso<R, NDIM, MODE, false>(maps, p, grid, stream);
@@ -55,18 +53,18 @@ static cudaError_t launch_modes(int mode, const StepMaps& maps, const StepParams
   }
 }
 
-template <int R, int NDIM>
+template <int R, int NDIM, bool ISO>
 static int smem_modes(int mode) {
   switch (mode) {
-    case MODE_PLAIN: return StepLayout<R, NDIM, MODE_PLAIN>::SMEM;
-    case MODE_SNAP_F32: return StepLayout<R, NDIM, MODE_SNAP_F32>::SMEM;
-    case MODE_SNAP_BF16: return StepLayout<R, NDIM, MODE_SNAP_BF16>::SMEM;
-    case MODE_SNAP_F16: return StepLayout<R, NDIM, MODE_SNAP_F16>::SMEM;
-    case MODE_GRAD_F32: return StepLayout<R, NDIM, MODE_GRAD_F32>::SMEM;
-    case MODE_GRAD_BF16: return StepLayout<R, NDIM, MODE_GRAD_BF16>::SMEM;
-    case MODE_GRAD_F16: return StepLayout<R, NDIM, MODE_GRAD_F16>::SMEM;
-    case MODE_BORN_SRC: return StepLayout<R, NDIM, MODE_BORN_SRC>::SMEM;
-    case MODE_SRC: return StepLayout<R, NDIM, MODE_SRC>::SMEM;
+    case MODE_PLAIN: return StepLayout<R, NDIM, MODE_PLAIN, ISO>::SMEM;
+    case MODE_SNAP_F32: return StepLayout<R, NDIM, MODE_SNAP_F32, ISO>::SMEM;
+    case MODE_SNAP_BF16: return StepLayout<R, NDIM, MODE_SNAP_BF16, ISO>::SMEM;
+    case MODE_SNAP_F16: return StepLayout<R, NDIM, MODE_SNAP_F16, ISO>::SMEM;
+    case MODE_GRAD_F32: return StepLayout<R, NDIM, MODE_GRAD_F32, ISO>::SMEM;
+    case MODE_GRAD_BF16: return StepLayout<R, NDIM, MODE_GRAD_BF16, ISO>::SMEM;
+    case MODE_GRAD_F16: return StepLayout<R, NDIM, MODE_GRAD_F16, ISO>::SMEM;
+    case MODE_BORN_SRC: return StepLayout<R, NDIM, MODE_BORN_SRC, ISO>::SMEM;
+    case MODE_SRC: return StepLayout<R, NDIM, MODE_SRC, ISO>::SMEM;
     default: return -1;
   }
 }
@@ -80,5 +78,9 @@ static int smem_modes(int mode) {
                                 cudaStream_t s) {                                                       \
     return ndim == 3 ? launch_modes<RR, 3>(mode, maps, p, grid, s) : launch_modes<RR, 2>(mode, maps, p, grid, s); \
   }                                                                                                     \
-  int step_smem_r##RR(int ndim, int mode) { return ndim == 3 ? smem_modes<RR, 3>(mode) : smem_modes<RR, 2>(mode); } \
+  int step_smem_r##RR(int ndim, int mode, bool iso) {                                                   \
+    if (iso_kernel(RR, iso))                                                                            \
+      return ndim == 3 ? smem_modes<RR, 3, true>(mode) : smem_modes<RR, 2, true>(mode);                 \
+    return ndim == 3 ? smem_modes<RR, 3, false>(mode) : smem_modes<RR, 2, false>(mode);                 \
+  }                                                                                                     \
   }

@@ -388,9 +388,10 @@ int prepare(wave_context* ctx, const wave_geometry* geom, float dt, int nt, int 
     sp.cy[j - 1] = static_cast<float>(w * inv_h2[1]);
     sp.cz[j - 1] = static_cast<float>(w * inv_h2[2]);
   }
-  sp.iso = 1;
+  bool equal = true;
   for (int j = 0; j < P->R; ++j)
-    if (sp.cx[j] != sp.cy[j] || (nd == 3 && sp.cy[j] != sp.cz[j])) sp.iso = 0;
+    if (sp.cx[j] != sp.cy[j] || (nd == 3 && sp.cy[j] != sp.cz[j])) equal = false;
+  sp.iso = iso_kernel(P->R, equal) ? 1 : 0;
   sp.nblx = g.nblx;
   sp.nbly = g.nbly;
   sp.nblz = g.nblz;
@@ -404,7 +405,7 @@ int prepare(wave_context* ctx, const wave_geometry* geom, float dt, int nt, int 
   sp.status = ctx->d_status;
   // grid: x tiles, axis-1 tiles, chunks of the streamed axis
   const int tx = (g.NX + step_bx() - 1) / step_bx();
-  const int ty = (g.NY + step_by(P->R, nd) - 1) / step_by(P->R, nd);
+  const int ty = (g.NY + step_by(P->R, nd, sp.iso != 0) - 1) / step_by(P->R, nd, sp.iso != 0);
   int chunks = 1;
   if (nd == 3) {
     const long long tiles = static_cast<long long>(tx) * ty;
@@ -465,7 +466,7 @@ int setup_model(wave_context* ctx, Prob& P, const float* m_dev, float* cm, cudaS
 int make_field_maps(wave_context* ctx, Prob& P, float* fields, int nslots, float* cm, float* grad, Work* W) {
   const GridDims& g = P.g;
   const int hx = step_hx(P.R);
-  const int by = step_by(P.R, P.ndim);
+  const int by = step_by(P.R, P.ndim, P.sp.iso != 0);
   const int bx = step_bx();
   {
     cuuint64_t dims[4] = {(cuuint64_t)g.NX, (cuuint64_t)g.NY, (cuuint64_t)g.NZ, (cuuint64_t)nslots};
@@ -514,7 +515,7 @@ int snapshot_map(wave_context* ctx, Prob& P, int fmt, void* store, int levels, C
   const int es = fmt == 0 ? 4 : 2;
   cuuint64_t dims[4] = {(cuuint64_t)g.NX, (cuuint64_t)g.NY, (cuuint64_t)g.NZ, (cuuint64_t)levels};
   cuuint64_t str[3] = {(cuuint64_t)g.pitch * es, (cuuint64_t)g.pitch * g.NY * es, (cuuint64_t)P.slot_elems * es};
-  cuuint32_t box[4] = {(cuuint32_t)step_bx(), (cuuint32_t)step_by(P.R, P.ndim), 1, 1};
+  cuuint32_t box[4] = {(cuuint32_t)step_bx(), (cuuint32_t)step_by(P.R, P.ndim, P.sp.iso != 0), 1, 1};
   const CUtensorMapDataType dt = fmt == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                           : (fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
   return make_map(ctx, map, dt, 4, store, dims, str, box);
@@ -1005,7 +1006,7 @@ int born_impl(wave_context* ctx, const wave_geometry* geom, const float* m, cons
     const GridDims& g = P.g;
     cuuint64_t dims[3] = {(cuuint64_t)g.NX, (cuuint64_t)g.NY, (cuuint64_t)g.NZ};
     cuuint64_t str[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.pitch * g.NY * 4};
-    cuuint32_t box[3] = {(cuuint32_t)step_bx(), (cuuint32_t)step_by(P.R, P.ndim), 1};
+    cuuint32_t box[3] = {(cuuint32_t)step_bx(), (cuuint32_t)step_by(P.R, P.ndim, P.sp.iso != 0), 1};
     TRY(make_map(ctx, &maps_born.g, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, dmc, dims, str, box));
   }
   wave_points empty{0, nullptr};

@@ -53,25 +53,27 @@ constexpr int kSlabY = 2;
 // A CTA owns BX x BY output columns (x, axis 1) and streams a chunk of planes
 // along axis 2 (3D); in 2D it owns one BX x BY tile of the single plane.
 // ---------------------------------------------------------------------------
-#ifndef WAVE_LEAD_MIN_R
-#define WAVE_LEAD_MIN_R 7
-#endif
-#ifndef WAVE_BY14_MIN_R
-#define WAVE_BY14_MIN_R 8
-#endif
+// Radius from which the lead-plane design is used (every mode).
+constexpr int kLeadMinR = 7;
+// Radius from which equal spacing on every axis selects the kernel variant
+// with one coefficient per offset (measured faster from radius 7 on, slower at
+// radius 5-6, equal below).
+constexpr int kIsoMinR = 7;
+__host__ __device__ constexpr bool iso_kernel(int R, bool equal_spacing) { return equal_spacing && R >= kIsoMinR; }
 
 // Shared memory of one SM and the part the driver keeps per resident CTA.
 constexpr int kSmemPerSm = 228 * 1024;
 constexpr int kSmemReservedPerCta = 1024;
 constexpr int kSmemTwoCtas = kSmemPerSm / 2 - kSmemReservedPerCta;  // per CTA at two CTAs per SM
 
-template <int R, int NDIM>
+template <int R, int NDIM, bool ISO = false>
 struct StepTraits {
   static constexpr int BX = 64;                   // x outputs per CTA (16 threads x 4)
   // axis-1 outputs per CTA (one row per 16 threads, two rows per warp); 3D
-  // radius 8 uses 14 rows so that a CTA has 8 warps and two CTAs fit the
-  // register file at 128 registers per thread
-  static constexpr int BY = (NDIM == 3 && R >= WAVE_BY14_MIN_R) ? 14 : 16;
+  // radius 8, and radius 7 with the equal-spacing kernel, use 14 rows so that
+  // a CTA has 8 warps and two CTAs fit the register file at 128 registers per
+  // thread (measured slower for the general radius-7 kernel)
+  static constexpr int BY = (NDIM == 3 && (R >= 8 || (R == 7 && ISO))) ? 14 : 16;
   static constexpr int HX = (R <= 4) ? 4 : 8;     // x halo, rounded to 16 bytes for TMA
   static constexpr int RZ = (NDIM == 3) ? R : 0;  // halo along the streamed axis
   static constexpr int UW = BX + 2 * HX;          // smem row length of a halo box (floats)
@@ -85,10 +87,10 @@ struct StepTraits {
   static constexpr int NTHREADS = (NCW + 1) * 32; // + one producer warp
 };
 
-// Shared-memory layout, prefetch depth and occupancy of one (R, NDIM, MODE).
-template <int R, int NDIM, int MODE>
+// Shared-memory layout, prefetch depth and occupancy of one (R, NDIM, MODE, ISO).
+template <int R, int NDIM, int MODE, bool ISO = false>
 struct StepLayout {
-  using T = StepTraits<R, NDIM>;
+  using T = StepTraits<R, NDIM, ISO>;
   static constexpr int SNAP_ELEM = mode_snap_fmt(MODE) == 0 ? 4 : 2;
   // per-point tiles loaded with each plane: previous level, cm, and g (the
   // gradient, dm or S) and the snapshot where the mode needs them
@@ -106,7 +108,7 @@ struct StepLayout {
   // loaded again (from L2) with the per-point tiles, so the shared ring holds
   // only the prefetch depth instead of R+1+PF halo planes.  Used from radius 7
   // on, and wherever the classic design would not fit two CTAs per SM.
-  static constexpr bool LEAD = (NDIM == 3) && (R >= WAVE_LEAD_MIN_R || classic_smem(2) > kSmemTwoCtas);
+  static constexpr bool LEAD = (NDIM == 3) && (R >= kLeadMinR || classic_smem(2) > kSmemTwoCtas);
   // Deep variant (classic design, radius <= 5, not the imaging condition):
   // two CTAs per SM with a 4-plane prefetch and planes taken in pairs (half
   // the register-queue moves), which the 96 registers per thread at two CTAs
@@ -151,7 +153,7 @@ struct StepParams {
   // stencil coefficients (1/h^2 folded in): lap = c0*u + sum_j c{x,y,z}[j-1]*(u[-j]+u[+j])
   float c0;
   float cx[8], cy[8], cz[8];
-  int iso;                 // 1 when cx == cy (== cz): equal spacing on every axis
+  int iso;                 // 1: equal-spacing kernel variant (cx == cy (== cz), radius >= kIsoMinR)
   // sponge: eta = sum_axis eta_max_axis * (delta/nbl)^2 ; nbl per kernel axis (0 on a missing axis)
   int nblx, nbly, nblz;
   float emx, emy, emz;     // eta_max per axis divided by nbl^2 (1/ms)
@@ -177,12 +179,13 @@ struct StepMaps {
   CUtensorMap s;   // snapshot store, tile box (4D: x, y, z, level)
 };
 
+// Launches the step kernel variant of p.iso.
 cudaError_t launch_step(int R, int ndim, int mode, const StepMaps& maps, const StepParams& p,
                         dim3 grid, cudaStream_t stream);
-// Tile geometry of StepTraits<R, NDIM> for the host (maps and grid).
-int step_smem_bytes(int R, int ndim, int mode);
+// Tile geometry of StepTraits<R, NDIM, iso> for the host (maps and grid).
+int step_smem_bytes(int R, int ndim, int mode, bool iso);
 int step_bx();
-int step_by(int R, int ndim);
+int step_by(int R, int ndim, bool iso);
 int step_hx(int R);
 
 // ---------------------------------------------------------------------------

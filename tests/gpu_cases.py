@@ -56,8 +56,8 @@ def small3d(so, shape=(83, 21, 40), nbl=5, nt=60, seed=0, nsrc=2, nrec=25, spaci
     return og, m, dt, nt, so, src, q, rec
 
 
-def small2d(so, shape=(150, 77), nbl=9, nt=80, seed=1, nsrc=2, nrec=19):
-    og = oracle.model.Geometry(shape=shape, spacing=(7.5, 10.0), origin=(0.0, 0.0), nbl=nbl, sponge_vref=2.0)
+def small2d(so, shape=(150, 77), nbl=9, nt=80, seed=1, nsrc=2, nrec=19, spacing=(7.5, 10.0)):
+    og = oracle.model.Geometry(shape=shape, spacing=spacing, origin=(0.0, 0.0), nbl=nbl, sponge_vref=2.0)
     r = inputs.rng(seed)
     v = 1.5 + 0.5 * r.uniform(size=og.phys_array_shape)
     m = inputs.slowness2(v)

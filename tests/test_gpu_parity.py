@@ -53,9 +53,10 @@ def test_forward_3d_all_orders(ctx, so, iso):
     assert e_d <= 1e-4 and e_u <= 1e-4
 
 
-@pytest.mark.parametrize("so", [2, 4, 8, 12, 16])
-def test_forward_2d_all_orders(ctx, so):
-    og, m, dt, nt, so, src, q, rec = small2d(so)
+@pytest.mark.parametrize("so,iso", [(2, False), (4, False), (8, False), (12, False), (16, False), (14, True),
+                                    (16, True)])
+def test_forward_2d_all_orders(ctx, so, iso):
+    og, m, dt, nt, so, src, q, rec = small2d(so, spacing=(10.0, 10.0) if iso else (7.5, 10.0))
     _, geom = geometries(og)
     d = wave.wave_forward(ctx, geom, _dev(m), src, _dev(q), rec, dt, nt, so).cpu().numpy()
     ref = oracle.wave.forward(og, m, dt, nt, so, q, src, rec).d
@@ -101,11 +102,15 @@ def test_adjoint_and_dot_product(ctx, case):
     assert abs(lhs - rhs) <= 1e-4 * max(abs(lhs), abs(rhs))
 
 
-@pytest.mark.parametrize("case", ["3d8", "2d4", "3d10", "3d12", "3d16", "3d8iso", "3d14iso", "3d16iso"])
+@pytest.mark.parametrize("case", ["3d8", "2d4", "3d10", "3d12", "3d14", "3d16", "3d8iso", "3d14iso", "3d16iso",
+                                  "2d16iso"])
 def test_gradient_full_fp32(ctx, case):
     so = int(case[2:].replace("iso", ""))
-    h = (12.5, 12.5, 12.5) if case.endswith("iso") else (10.0, 12.0, 9.0)
-    og, m, dt, nt, so, src, q, rec = small3d(so, spacing=h) if case.startswith("3d") else small2d(so)
+    iso = case.endswith("iso")
+    if case.startswith("3d"):
+        og, m, dt, nt, so, src, q, rec = small3d(so, spacing=(12.5, 12.5, 12.5) if iso else (10.0, 12.0, 9.0))
+    else:
+        og, m, dt, nt, so, src, q, rec = small2d(so, spacing=(10.0, 10.0) if iso else (7.5, 10.0))
     _, geom = geometries(og)
     r = np.random.default_rng(9)
     d_obs = (oracle.wave.forward(og, m * 1.02, dt, nt, so, q, src, rec).d).astype(np.float32)
@@ -119,15 +124,15 @@ def test_gradient_full_fp32(ctx, case):
     del r
 
 
-@pytest.mark.parametrize("so", [10, 12])
-def test_gradient_fp16_snapshots_high_order(ctx, so):
-    og, m, dt, nt, so, src, q, rec = small3d(so)
+@pytest.mark.parametrize("so,iso", [(10, False), (12, False), (14, True), (16, True)])
+def test_gradient_fp16_snapshots_high_order(ctx, so, iso):
+    og, m, dt, nt, so, src, q, rec = small3d(so, spacing=(12.5, 12.5, 12.5) if iso else (10.0, 12.0, 9.0))
     _, geom = geometries(og)
     d_obs = (oracle.wave.forward(og, m * 1.02, dt, nt, so, q, src, rec).d).astype(np.float32)
     g, _ = wave.wave_gradient(ctx, geom, _dev(m), src, _dev(q), rec, _dev(d_obs), dt, nt, so, snap_mode="full_fp16")
     g_ref, _ = oracle.wave.gradient(og, m, dt, nt, so, q, src, rec, d_obs)
     e_g = rel_l2(g.cpu().numpy(), g_ref)
-    print("3D so%d gradient, FP16 snapshots: rel-L2 %.3e" % (so, e_g))
+    print("3D so%d%s gradient, FP16 snapshots: rel-L2 %.3e" % (so, " (equal spacing)" if iso else "", e_g))
     assert e_g <= 5e-4
 
 
