@@ -109,17 +109,18 @@ struct StepLayout {
   // only the prefetch depth instead of R+1+PF halo planes.  Used from radius 7
   // on, and wherever the classic design would not fit two CTAs per SM.
   static constexpr bool LEAD = (NDIM == 3) && (R >= kLeadMinR || classic_smem(2) > kSmemTwoCtas);
-  // Deep variant (classic design, radius <= 5, not the imaging condition):
-  // two CTAs per SM with a 4-plane prefetch and planes taken in pairs (half
-  // the register-queue moves), which the 96 registers per thread at two CTAs
-  // allow.  The imaging steps are HBM-bound and keep the 2-plane prefetch.
-  static constexpr bool DEEP =
-      NDIM == 3 && !LEAD && R <= 5 && !mode_is_grad(MODE) && classic_smem(4) <= kSmemTwoCtas;
-  static constexpr int PF = NDIM == 3 ? (DEEP ? 4 : 2) : 0;  // planes prefetched ahead
+  // Deep variant (classic design, not the imaging condition): two CTAs per SM
+  // with a 4-plane prefetch (3 where 4 would not fit two CTAs) and, up to
+  // radius 5, output planes taken in pairs (half the register-queue moves),
+  // which the 96 registers per thread at two CTAs allow.  The imaging steps
+  // are HBM-bound and keep the 2-plane prefetch.
+  static constexpr int DEEP_PF = classic_smem(4) <= kSmemTwoCtas ? 4 : (classic_smem(3) <= kSmemTwoCtas ? 3 : 0);
+  static constexpr bool DEEP = NDIM == 3 && !LEAD && !mode_is_grad(MODE) && DEEP_PF > 0;
+  static constexpr int PF = NDIM == 3 ? (DEEP ? DEEP_PF : 2) : 0;  // planes prefetched ahead
   static constexpr int NSU = LEAD ? PF + 1 : T::RZ + 1 + PF;  // queue-feed ring stages
   static constexpr int Q_BYTES = LEAD ? T::T_ELEMS * 4 : T::U_BYTES;
   static constexpr int Q_STRIDE = LEAD ? T::T_ELEMS * 4 : T::U_STRIDE;
-  static constexpr int QU = DEEP ? 2 : 1;  // output planes per register-queue move
+  static constexpr int QU = (DEEP && R <= 5) ? 2 : 1;  // output planes per register-queue move
   // resident CTAs per SM asked of the register allocator (registers per
   // thread follow the warps per SM sub-partition: 3 CTAs of 9 warps leave 72,
   // 2 of 9 leave 96, 2 of 8 leave 128)
