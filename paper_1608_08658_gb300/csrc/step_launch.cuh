@@ -13,6 +13,8 @@ template <int R, int NDIM, int MODE, bool ISO>
 static cudaError_t launch_iso(const StepMaps& maps, const StepParams& p, dim3 grid, cudaStream_t stream) {
   using T = StepTraits<R, NDIM, ISO>;
   using L = StepLayout<R, NDIM, MODE, ISO>;
+  static_assert(L::SMEM <= 227 * 1024, "step layout exceeds the shared memory of one CTA");
+  static_assert(L::SMEM <= kSmemTwoCtas || L::MIN_BLOCKS == 1, "step layout does not fit its CTAs per SM");
   // the dynamic shared-memory limit is a per-device function attribute
   static std::atomic<unsigned long long> configured{0};
   int device = 0;
