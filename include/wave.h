@@ -65,7 +65,7 @@ extern "C" {
 #define WAVE_ERR_OUT_OF_MEMORY  4  /* workspace would exceed the budget, or cudaMalloc failed */
 #define WAVE_ERR_CUDA           5  /* a CUDA runtime/driver call or kernel launch failed */
 #define WAVE_ERR_TIMEOUT        6  /* a bounded device-side wait expired (kernel gave up) */
-#define WAVE_ERR_NOT_SUPPORTED  7  /* feature/size not supported by this build or device */
+#define WAVE_ERR_NOT_SUPPORTED  7  /* feature or size not supported by the library or the device */
 
 typedef struct wave_context wave_context;
 
