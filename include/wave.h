@@ -80,7 +80,10 @@ typedef struct wave_context wave_context;
 typedef struct {
   int32_t ndim;          /* 2 or 3 */
   int32_t nbl;           /* absorbing points per side, >= 0 */
-  int64_t shape[3];      /* physical points per axis, x-first; shape[2] ignored in 2D */
+  int64_t shape[3];      /* physical points per axis, x-first, each in [2, 2^20]
+                            (WAVE_ERR_INVALID_ARG otherwise); shape[2] ignored in 2D.
+                            A grid whose axis 1 needs more than 65535 CTA tiles of 14-16
+                            rows is WAVE_ERR_NOT_SUPPORTED. */
   double spacing[3];     /* grid spacing per axis, m, > 0 */
   double origin[3];      /* coordinate of physical node 0 per axis, m */
   double sponge_vref;    /* km/s, > 0 when nbl > 0 */
