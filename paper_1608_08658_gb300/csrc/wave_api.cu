@@ -73,6 +73,10 @@ struct wave_context {
   double ms[WAVE_KERNEL_KINDS] = {};
   int ckpt_interval = 0;
   int last_plan[4] = {0, 0, 0, 0};  // fmt, buffer levels, parts per segment, segments
+  // side stream and events that copy finished receiver rows to a pinned host
+  // buffer while later time steps run (created on first use)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_rows = nullptr, ev_copied = nullptr;
 };
 
 namespace {
@@ -203,6 +207,7 @@ struct OutStage {
   void* dev = nullptr;
   size_t bytes = 0;
   bool copy_back = false;
+  bool pinned = false;  // the host buffer is page-locked: copies to it are asynchronous
 };
 
 int stage_out(wave_context* ctx, const char* name, void* p, size_t bytes, OutStage* o) {
@@ -220,6 +225,12 @@ int stage_out(wave_context* ctx, const char* name, void* p, size_t bytes, OutSta
   }
   TRY(ws_get(ctx, std::string("out_") + name, bytes, &o->dev));
   o->copy_back = true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) == cudaSuccess) {
+    o->pinned = a.type == cudaMemoryTypeHost;
+  } else {
+    cudaGetLastError();
+  }
   return WAVE_OK;
 }
 
@@ -807,6 +818,35 @@ int forward_steps(wave_context* ctx, Prob& P, Work& W, int n0, int n1, const flo
   return WAVE_OK;
 }
 
+// Forward steps 0 .. nt-2 with the receiver rows copied to the caller's pinned
+// host buffer in chunks on a side stream, overlapping the copies with the
+// remaining steps; `s` waits for the last copy before the call returns.
+int forward_steps_streamed(wave_context* ctx, Prob& P, Work& W, int nt, const float* q, PointSetDev* src,
+                           PointSetDev* rec, const OutStage& dout, cudaStream_t s) {
+  constexpr int kChunk = 128;  // time steps per copied block of rows
+  if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  if (!ctx->ev_rows) CK(cudaEventCreateWithFlags(&ctx->ev_rows, cudaEventDisableTiming));
+  if (!ctx->ev_copied) CK(cudaEventCreateWithFlags(&ctx->ev_copied, cudaEventDisableTiming));
+  const size_t row_bytes = static_cast<size_t>(rec->n) * sizeof(float);
+  float* d = static_cast<float*>(dout.dev);
+  long long rows_done = 0;
+  for (int n0 = 0; n0 < nt - 1; n0 += kChunk) {
+    const int n1 = std::min(n0 + kChunk, nt - 1);
+    TRY(forward_steps(ctx, P, W, n0, n1, q, src, d, rec, nullptr, 0, 0, s));
+    const long long rows_ready = n1 + 1;  // rows 0 .. n1 are final
+    CK(cudaEventRecord(ctx->ev_rows, s));
+    CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_rows, 0));
+    CK(cudaMemcpyAsync(static_cast<char*>(dout.user) + rows_done * row_bytes,
+                       reinterpret_cast<const char*>(d) + rows_done * row_bytes,
+                       static_cast<size_t>(rows_ready - rows_done) * row_bytes, cudaMemcpyDeviceToHost,
+                       ctx->copy_stream));
+    rows_done = rows_ready;
+  }
+  CK(cudaEventRecord(ctx->ev_copied, ctx->copy_stream));
+  CK(cudaStreamWaitEvent(s, ctx->ev_copied, 0));
+  return WAVE_OK;
+}
+
 int store_level(wave_context* ctx, Prob& P, Work& W, int slot, SnapStore* S, int k, cudaStream_t s) {
   return launch(ctx, WAVE_KERNEL_OTHER, s, [&] {
     return launch_snapshot_store(P.g, slot_ptr(W, P, slot), S->level(P, k), S->level_scale(P, k), S->fmt, P.slabs_x,
@@ -917,8 +957,12 @@ int forward_impl(wave_context* ctx, const wave_geometry* geom, const float* m, c
     GatherSet grec = gather_set(P, Rr);
     TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_gather(grec, slot_ptr(W, P, fslot(0)), d, s); }));
   }
-  TRY(forward_steps(ctx, P, W, 0, nt - 1, static_cast<const float*>(qdev), S, d, Rr, nullptr, 0, 0, s));
-  TRY(finish_out(ctx, dout, s));
+  if (dout.copy_back && dout.pinned) {
+    TRY(forward_steps_streamed(ctx, P, W, nt, static_cast<const float*>(qdev), S, Rr, dout, s));
+  } else {
+    TRY(forward_steps(ctx, P, W, 0, nt - 1, static_cast<const float*>(qdev), S, d, Rr, nullptr, 0, 0, s));
+    TRY(finish_out(ctx, dout, s));
+  }
   for (int k = 0; k < 2; ++k) {
     float* fin = k == 0 ? u_final_prev : u_final;
     if (!fin) continue;
@@ -1496,6 +1540,9 @@ int wave_context_destroy(wave_context* ctx) {
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->h_minmax) cudaFreeHost(ctx->h_minmax);
   if (ctx->h_phi) cudaFreeHost(ctx->h_phi);
+  if (ctx->ev_rows) cudaEventDestroy(ctx->ev_rows);
+  if (ctx->ev_copied) cudaEventDestroy(ctx->ev_copied);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   cudaGetLastError();
   delete ctx;
   return WAVE_OK;

@@ -237,6 +237,17 @@ def test_host_buffers_match_device_buffers(ctx):
     np.testing.assert_array_equal(d_host, d_dev)
 
 
+def test_pinned_host_output_streamed_in_chunks(ctx):
+    """A page-locked host output is filled by chunked copies that overlap the
+    time steps (128 steps per chunk; nt = 300 gives a ragged last chunk)."""
+    og, m, dt, _, so, src, q, rec = small3d(8, nt=300)
+    _, geom = geometries(og)
+    d_dev = wave.wave_forward(ctx, geom, _dev(m), src, _dev(q), rec, dt, 300, so)
+    d_pin = torch.empty((300, len(rec)), dtype=torch.float32, pin_memory=True)
+    wave.wave_forward(ctx, geom, _dev(m), src, _dev(q), rec, dt, 300, so, d_out=d_pin)
+    assert torch.equal(d_pin, d_dev.cpu())
+
+
 def test_errors_are_reported(ctx):
     og, m, dt, nt, so, src, q, rec = small2d(4)
     _, geom = geometries(og)
