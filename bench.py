@@ -57,8 +57,9 @@ def parse_args():
     ap.add_argument("--requests", type=int, default=400, help="serve mode: number of requests")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serve mode: HBM budget for resident requests")
     ap.add_argument("--max-resident", type=int, default=32, help="serve mode: stream slots")
-    ap.add_argument("--workload", default="throughput", choices=["throughput", "paper_demo", "large"],
-                    help="throughput: 512^3 two-layer + perturbation (default); paper_demo: the paper's 3D "
+    ap.add_argument("--workload", default="throughput", choices=["throughput", "fwi", "paper_demo", "large"],
+                    help="throughput: 512^3 two-layer + perturbation (default); fwi: 256^3 + 40, h = 12.5 m, "
+                         "v(z) background with Gaussian anomalies, order 8, nt 1500; paper_demo: the paper's 3D "
                          "demonstration shape 201x201x70 + 40 (h = 15 m, order 14, 1 s, 10 Hz); large: "
                          "1000x1000x600 + 40, order 16, layered model with a salt body")
     ap.add_argument("--no-e2e", action="store_true")
@@ -84,6 +85,16 @@ def make_workload(n, nbl, so, nt, kind="throughput"):
         rec = inputs.surface_grid_receivers(shape[0], shape[1], h[:2], 30.0)
         return dict(shape=shape, spacing=h, nbl=40, so=14, nt=nt, v0=v0, v_true=v0, src=src, rec=rec,
                     vmax=float(v0.max()), f0=0.010, duration_ms=1000.0, kind=kind)
+    if kind == "fwi":
+        # FWI gradient workload: background v(z) = 1.5 + 0.6 z[km] (the starting model), true model with three
+        # seeded Gaussian anomalies; 128 x 128 receivers on every second node at 25 m; Ricker 10 Hz
+        shape, h = (256, 256, 256), (12.5, 12.5, 12.5)
+        v0, vt = inputs.gradient_models(shape, h)
+        ext = (shape[0] - 1) * h[0]
+        src = np.array([[0.5 * ext, 0.5 * ext, 25.0]], dtype=np.float32)
+        rec = inputs.surface_grid_receivers(shape[0] // 2, shape[1] // 2, (2 * h[0], 2 * h[1]), 25.0)
+        return dict(shape=shape, spacing=h, nbl=40, so=8, nt=1500, v0=v0, v_true=vt, src=src, rec=rec,
+                    vmax=float(vt.max()), f0=0.010, kind=kind)
     if kind == "large":
         shape, h = (1000, 1000, 600), (10.0, 10.0, 10.0)
         v0 = inputs.layered_salt_velocity(shape, h)
@@ -111,11 +122,14 @@ def workload_config(w, snap, mode="gradient"):
     if w.get("kind", "throughput") != "throughput":
         comp = [s + 2 * w["nbl"] for s in w["shape"]]
         name = {"paper_demo": "paper 3D demonstration shape (Sec. V-D), synthetic layered model",
+                "fwi": "starting model v(z) = 1.5 + 0.6 z km/s, true model with three Gaussian anomalies",
                 "large": "large layered model with salt body"}[w["kind"]]
         return {"workload": "3D %s %s: %s + %d sponge = %s points, h=%g m, so=%d, nt=%d" % (
                     what, name, "x".join(map(str, w["shape"])), w["nbl"], "x".join(map(str, comp)), w["spacing"][0],
                     w["so"], w["nt"]),
                 "grid": list(w["shape"]), "nbl": w["nbl"], "space_order": w["so"], "nt": w["nt"], "snap_mode": snap,
+                "points_per_step": ("2 * %s * (nt-1) (forward + adjoint updates)" if mode == "gradient"
+                                    else "%s * (nt-1)") % "x".join(map(str, comp)),
                 "l2": "inputs larger than L2" if np.prod(comp) * 4 > 129e6 else "fields smaller than L2"}
     return {
         "workload": "3D " + what + " %d^3 (+%d sponge = %d^3), h=10 m, so=%d, nt=%d, two-layer 1.5/2.5 km/s + 5%% "

@@ -339,13 +339,14 @@ WAVE_API int wave_objective_noalloc(const float* d, const float* d_obs, float* r
 #define WAVE_KERNEL_OTHER       4  /* set-up, residual, fold, snapshot store, copies */
 #define WAVE_KERNEL_KINDS       5
 
-/* Enable (1) or disable (0) per-launch CUDA-event timing of the context's
- * kernels on the stream they are launched on.  Disabled by default. */
+/* Enable (1) or disable (0) CUDA-event timing of the context's kernels on the
+ * stream they are launched on: every 4th launch of each kind (the first, the
+ * fifth, ...) is bracketed by a pair of timing events.  Disabled by default. */
 WAVE_API int wave_context_set_profiling(wave_context* ctx, int enable);
 
-/* Launch count (always counted) and summed event time in ms (when profiling)
- * of one kernel kind since the last reset; totals over all kinds when
- * kind < 0. */
+/* Launch count (always counted) and total time in ms of one kernel kind since
+ * the last reset: the mean event time of its timed launches times its launch
+ * count (0 when none was timed); totals over all kinds when kind < 0. */
 WAVE_API int wave_context_kernel_stats(wave_context* ctx, int kind, int64_t* launches, double* total_ms);
 WAVE_API int wave_context_reset_stats(wave_context* ctx);
 

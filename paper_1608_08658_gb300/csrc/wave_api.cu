@@ -70,7 +70,8 @@ struct wave_context {
   std::vector<cudaEvent_t> ev_free;
   std::vector<Pending> pending;
   int64_t launches[WAVE_KERNEL_KINDS] = {};
-  double ms[WAVE_KERNEL_KINDS] = {};
+  int64_t timed[WAVE_KERNEL_KINDS] = {};  // launches whose duration was taken with events
+  double ms[WAVE_KERNEL_KINDS] = {};      // summed duration of the timed launches
   int ckpt_interval = 0;
   int last_plan[4] = {0, 0, 0, 0};  // fmt, buffer levels, parts per segment, segments
   // side stream and events that copy finished receiver rows to a pinned host
@@ -253,9 +254,13 @@ cudaEvent_t take_event(wave_context* ctx) {
 
 template <class F>
 int launch(wave_context* ctx, int kind, cudaStream_t s, F&& f) {
-  ctx->launches[kind]++;
+  // with profiling on, every kProfileEvery-th launch of a kind is bracketed by
+  // a pair of timing events (events on every launch add a few microseconds
+  // of front-end work per kernel to the measured stream)
+  constexpr int64_t kProfileEvery = 4;
+  const int64_t index = ctx->launches[kind]++;
   cudaError_t e;
-  if (ctx->profiling) {
+  if (ctx->profiling && index % kProfileEvery == 0) {
     Pending pd{kind, take_event(ctx), take_event(ctx)};
     cudaEventRecord(pd.a, s);
     e = f();
@@ -274,7 +279,10 @@ int launch(wave_context* ctx, int kind, cudaStream_t s, F&& f) {
 void collect_events(wave_context* ctx) {
   for (auto& pd : ctx->pending) {
     float t = 0.f;
-    if (cudaEventElapsedTime(&t, pd.a, pd.b) == cudaSuccess) ctx->ms[pd.kind] += t;
+    if (cudaEventElapsedTime(&t, pd.a, pd.b) == cudaSuccess) {
+      ctx->ms[pd.kind] += t;
+      ctx->timed[pd.kind]++;
+    }
     cudaGetLastError();
     ctx->ev_free.push_back(pd.a);
     ctx->ev_free.push_back(pd.b);
@@ -1717,7 +1725,8 @@ int wave_context_kernel_stats(wave_context* ctx, int kind, int64_t* launches, do
   for (int k = 0; k < WAVE_KERNEL_KINDS; ++k) {
     if (kind < 0 || k == kind) {
       l += ctx->launches[k];
-      t += ctx->ms[k];
+      // the timed launches sample the kind: scale their mean to all launches
+      if (ctx->timed[k] > 0) t += ctx->ms[k] * static_cast<double>(ctx->launches[k]) / ctx->timed[k];
     }
   }
   if (launches) *launches = l;
@@ -1855,6 +1864,7 @@ int wave_context_reset_stats(wave_context* ctx) {
   if (!ctx) return WAVE_ERR_INVALID_ARG;
   for (int k = 0; k < WAVE_KERNEL_KINDS; ++k) {
     ctx->launches[k] = 0;
+    ctx->timed[k] = 0;
     ctx->ms[k] = 0;
   }
   return WAVE_OK;
