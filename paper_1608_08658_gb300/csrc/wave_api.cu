@@ -77,7 +77,7 @@ struct wave_context {
   // side stream and events that copy finished receiver rows to a pinned host
   // buffer while later time steps run (created on first use)
   cudaStream_t copy_stream = nullptr;
-  cudaEvent_t ev_rows = nullptr, ev_copied = nullptr;
+  cudaEvent_t ev_rows = nullptr, ev_copied = nullptr, ev_input = nullptr;
 };
 
 namespace {
@@ -200,6 +200,45 @@ int stage_in(wave_context* ctx, const char* name, const void* p, size_t bytes, c
   TRY(ws_get(ctx, std::string("in_") + name, bytes, &d));
   CK(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, s));
   *out = d;
+  return WAVE_OK;
+}
+
+int ensure_copy_stream(wave_context* ctx) {
+  if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+  if (!ctx->ev_rows) CK(cudaEventCreateWithFlags(&ctx->ev_rows, cudaEventDisableTiming));
+  if (!ctx->ev_copied) CK(cudaEventCreateWithFlags(&ctx->ev_copied, cudaEventDisableTiming));
+  if (!ctx->ev_input) CK(cudaEventCreateWithFlags(&ctx->ev_input, cudaEventDisableTiming));
+  return WAVE_OK;
+}
+
+// Input first needed late in the call (observed data, adjoint sources): a
+// page-locked host array is copied on the side stream, overlapping the work
+// enqueued on `s` meanwhile, and *deferred tells the caller to make `s` wait
+// on ctx->ev_input before the first use.  Other arrays go through stage_in.
+int stage_in_deferred(wave_context* ctx, const char* name, const void* p, size_t bytes, cudaStream_t s,
+                      const void** out, bool* deferred) {
+  *deferred = false;
+  bool dev = false;
+  if (bytes > 0) TRY(classify(ctx, p, &dev));
+  cudaPointerAttributes a;
+  bool pinned = false;
+  if (bytes > 0 && !dev) {
+    if (cudaPointerGetAttributes(&a, p) == cudaSuccess) {
+      pinned = a.type == cudaMemoryTypeHost;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  if (!pinned) return stage_in(ctx, name, p, bytes, s, out);
+  TRY(ensure_copy_stream(ctx));
+  void* d = nullptr;
+  TRY(ws_get(ctx, std::string("in_") + name, bytes, &d));
+  CK(cudaEventRecord(ctx->ev_input, s));  // after earlier work on s that may still read the buffer
+  CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_input, 0));
+  CK(cudaMemcpyAsync(d, p, bytes, cudaMemcpyHostToDevice, ctx->copy_stream));
+  CK(cudaEventRecord(ctx->ev_input, ctx->copy_stream));
+  *out = d;
+  *deferred = true;
   return WAVE_OK;
 }
 
@@ -832,9 +871,7 @@ int forward_steps(wave_context* ctx, Prob& P, Work& W, int n0, int n1, const flo
 int forward_steps_streamed(wave_context* ctx, Prob& P, Work& W, int nt, const float* q, PointSetDev* src,
                            PointSetDev* rec, const OutStage& dout, cudaStream_t s) {
   constexpr int kChunk = 128;  // time steps per copied block of rows
-  if (!ctx->copy_stream) CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
-  if (!ctx->ev_rows) CK(cudaEventCreateWithFlags(&ctx->ev_rows, cudaEventDisableTiming));
-  if (!ctx->ev_copied) CK(cudaEventCreateWithFlags(&ctx->ev_copied, cudaEventDisableTiming));
+  TRY(ensure_copy_stream(ctx));
   const size_t row_bytes = static_cast<size_t>(rec->n) * sizeof(float);
   float* d = static_cast<float*>(dout.dev);
   long long rows_done = 0;
@@ -1205,7 +1242,10 @@ int gradient_impl(wave_context* ctx, const wave_geometry* geom, const float* m, 
   const void* qdev = nullptr;
   if (ns > 0) TRY(stage_in(ctx, "q", q, static_cast<size_t>(nt) * ns * 4, s, &qdev));
   const void* obs = nullptr;
-  if (nr > 0) TRY(stage_in(ctx, y_given ? "y" : "dobs", y_given ? y_given : d_obs, static_cast<size_t>(nt) * nr * 4, s, &obs));
+  bool obs_deferred = false;
+  if (nr > 0)
+    TRY(stage_in_deferred(ctx, y_given ? "y" : "dobs", y_given ? y_given : d_obs, static_cast<size_t>(nt) * nr * 4, s,
+                          &obs, &obs_deferred));
   Work W;
   TRY(prepare_fields(ctx, P, static_cast<const float*>(mdev), s, true, &W));
   wave_points empty{0, nullptr};
@@ -1265,6 +1305,8 @@ int gradient_impl(wave_context* ctx, const wave_geometry* geom, const float* m, 
   const int n_first = nseg > 0 ? std::min(nseg * S, T0) : 0;
   TRY(forward_steps(ctx, P, W, n_first, nt - 1, qd, Sp, d, Rr, &SS, T0, T0, s));
   TRY(store_level(ctx, P, W, fslot(nt - 1), &SS, nt - 1 - T0, s));
+  // the observed data (or adjoint sources) were uploaded during the forward sweep
+  if (obs_deferred) CK(cudaStreamWaitEvent(s, ctx->ev_input, 0));
   // residual and objective
   if (nr > 0 && !y_given) {
     const long long n = static_cast<long long>(nt) * nr;
@@ -1550,6 +1592,7 @@ int wave_context_destroy(wave_context* ctx) {
   if (ctx->h_phi) cudaFreeHost(ctx->h_phi);
   if (ctx->ev_rows) cudaEventDestroy(ctx->ev_rows);
   if (ctx->ev_copied) cudaEventDestroy(ctx->ev_copied);
+  if (ctx->ev_input) cudaEventDestroy(ctx->ev_input);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   cudaGetLastError();
   delete ctx;

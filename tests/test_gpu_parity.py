@@ -248,6 +248,21 @@ def test_pinned_host_output_streamed_in_chunks(ctx):
     assert torch.equal(d_pin, d_dev.cpu())
 
 
+def test_pinned_host_inputs_uploaded_during_the_forward_sweep(ctx):
+    """Page-locked observed data is uploaded on a side stream while the forward
+    sweep runs; the gradient equals the one from device buffers bit for bit."""
+    og, m, dt, _, so, src, q, rec = small3d(8, nt=70)
+    _, geom = geometries(og)
+    d_obs = oracle.wave.forward(og, m * 1.02, dt, 70, so, q, src, rec).d.astype(np.float32)
+    g_dev, phi_dev = wave.wave_gradient(ctx, geom, _dev(m), src, _dev(q), rec, _dev(d_obs), dt, 70, so,
+                                        snap_mode="full_fp32")
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+    g_pin = torch.empty(m.shape, dtype=torch.float32).pin_memory()
+    _, phi_pin = wave.wave_gradient(ctx, geom, pin(m), pin(src), pin(q), pin(rec), pin(d_obs), dt, 70, so,
+                                    snap_mode="full_fp32", grad_out=g_pin)
+    assert torch.equal(g_pin, g_dev.cpu()) and phi_pin == phi_dev
+
+
 def test_errors_are_reported(ctx):
     og, m, dt, nt, so, src, q, rec = small2d(4)
     _, geom = geometries(og)
