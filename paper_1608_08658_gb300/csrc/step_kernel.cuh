@@ -10,13 +10,15 @@
 //   g -= u^j * (lam_{j-1} - 2 lam_j + lam_{j+1}) / dt^2 .
 //
 // Data movement (3D): a CTA owns a BX x BY column tile and streams a chunk of
-// planes along axis 2.  A producer warp issues TMA tile loads: each plane of
-// the centre level with its x/y halo into a ring of NSU stages, and the
-// per-point tiles (previous level, cm, and for the gradient g and the
-// snapshot) into a ring of NSP stages; mbarriers carry the transaction
-// counts.  Eight consumer warps keep the 2R+1 centre-level values of their
-// columns in a register queue (the z taps), read x/y taps from the centre
-// plane in shared memory, and write the new level with 16-byte stores.
+// planes along axis 2.  A producer warp issues TMA tile loads into two rings
+// of mbarrier-tracked stages: the queue-feed ring (halo planes of the centre
+// level in the classic layout; interior boxes of plane z+R in the lead-plane
+// layout) and the per-point ring (previous level, cm, and g / snapshot / dm /
+// S by mode; plus the centre halo box in the lead-plane layout).  BY/2
+// consumer warps keep the 2R+1 centre-level values of their columns in a
+// register queue (the z taps), read x/y taps from shared memory, and write the
+// new level with 16-byte stores.  The layout, prefetch depth, plane grouping
+// and occupancy of each (R, NDIM, MODE, ISO) are set by StepLayout.
 // Zero ghost values outside the grid come from the TMA out-of-bounds fill.
 // Every barrier wait is bounded; on expiry the kernel records a timeout in the
 // status word, drains its own copies and returns.
@@ -25,8 +27,6 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
-
-
 #include "ptx.cuh"
 #include "wave_internal.h"
 
@@ -34,17 +34,6 @@ namespace wave {
 namespace dev {
 
 __device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
-
-__device__ __forceinline__ void fma4(float4& acc, float c, const float4& a, const float4& b) {
-  acc.x = fmaf(c, a.x + b.x, acc.x);
-  acc.y = fmaf(c, a.y + b.y, acc.y);
-  acc.z = fmaf(c, a.z + b.z, acc.z);
-  acc.w = fmaf(c, a.w + b.w, acc.w);
-}
-
-__device__ __forceinline__ float get(const float4& v, int i) {
-  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
-}
 
 // 1/(1+k) and 1-k of the damped update.  1+k >= 1 is a moderate number, for
 // which the fast division intrinsic is within 2 ulp; the correctly rounded
@@ -114,8 +103,8 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
   uint64_t* fullU = reinterpret_cast<uint64_t*>(smem);
   uint64_t* emptyU = fullU + L::NSU;
   uint64_t* fullP = emptyU + L::NSU;
-  uint64_t* emptyP = fullP + T::NSP;
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(emptyP + T::NSP);
+  uint64_t* emptyP = fullP + L::NSP;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(emptyP + L::NSP);
   float* Ubase = reinterpret_cast<float*>(smem + L::U_OFF);
   unsigned char* Pbase = smem + L::PST_OFF;
 
@@ -135,7 +124,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
       mbar_init(&fullU[i], 1);
       mbar_init(&emptyU[i], T::NCW);
     }
-    for (int i = 0; i < T::NSP; ++i) {
+    for (int i = 0; i < L::NSP; ++i) {
       mbar_init(&fullP[i], 1);
       mbar_init(&emptyP[i], T::NCW);
     }
@@ -166,8 +155,8 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
         issuedU = s + 1;
         if (s >= 2 * RZ) {
           const int j = s - 2 * RZ;
-          const int ps = j % T::NSP;
-          if (j >= T::NSP) ok = mbar_wait_bounded(&emptyP[ps], ((j / T::NSP) - 1) & 1, abort_flag, kWaitLimitNs);
+          const int ps = j % L::NSP;
+          if (j >= L::NSP) ok = mbar_wait_bounded(&emptyP[ps], ((j / L::NSP) - 1) & 1, abort_flag, kWaitLimitNs);
           if (!ok) break;
           unsigned char* pd = Pbase + ps * L::P_BYTES;
           mbar_arrive_expect_tx(&fullP[ps], L::P_TX);
@@ -192,10 +181,10 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
             mbar_wait_bounded(&fullU[slot], (last / L::NSU) & 1, nullptr, kWaitLimitNs);
           }
         }
-        for (int slot = 0; slot < T::NSP; ++slot) {
+        for (int slot = 0; slot < L::NSP; ++slot) {
           if (issuedP > slot) {
-            const int last = slot + T::NSP * ((issuedP - 1 - slot) / T::NSP);
-            mbar_wait_bounded(&fullP[slot], (last / T::NSP) & 1, nullptr, kWaitLimitNs);
+            const int last = slot + L::NSP * ((issuedP - 1 - slot) / L::NSP);
+            mbar_wait_bounded(&fullP[slot], (last / L::NSP) & 1, nullptr, kWaitLimitNs);
           }
         }
       }
@@ -490,7 +479,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
       ring_un = 0;
       phase_un ^= 1u;
     }
-    if (++ring_ps == T::NSP) {
+    if (++ring_ps == L::NSP) {
       ring_ps = 0;
       phase_ps ^= 1u;
     }

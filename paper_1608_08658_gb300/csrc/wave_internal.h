@@ -81,8 +81,6 @@ struct StepTraits {
   static constexpr int U_BYTES = UW * UH * 4;                // bytes of one halo box
   static constexpr int U_STRIDE = (U_BYTES + 127) / 128 * 128;  // halo box spacing (128-byte aligned)
   static constexpr int T_ELEMS = BX * BY;
-  // per-plane ring: per-point tiles (+ the centre halo box in the lead design)
-  static constexpr int NSP = (NDIM == 3) ? 3 : 1;
   static constexpr int NCW = BY / 2;              // consumer warps
   static constexpr int NTHREADS = (NCW + 1) * 32; // + one producer warp
 };
@@ -96,30 +94,42 @@ struct StepLayout {
   // gradient, dm or S) and the snapshot where the mode needs them
   static constexpr int TILE_BYTES = mode_is_grad(MODE) ? (3 * T::T_ELEMS * 4 + T::T_ELEMS * SNAP_ELEM)
                                                        : (mode_loads_g(MODE) ? 3 : 2) * T::T_ELEMS * 4;
+  // Shared memory of a layout: `lead` selects the design, pf planes are
+  // prefetched ahead, nsp stages hold the per-point tiles.
+  //  * classic: the queue-feed ring holds halo planes z .. z+R+pf;
+  //  * lead-plane: the register queue is fed from a small ring of interior
+  //    boxes of plane z+R, and the halo box of the centre plane is loaded again
+  //    (from L2) with the per-point tiles, so the shared ring holds only the
+  //    prefetch depth instead of R+1+pf halo planes.
+  static constexpr int nsu_of(bool lead, int pf) { return lead ? pf + 1 : T::RZ + 1 + pf; }
+  static constexpr int qstride_of(bool lead) { return lead ? T::T_ELEMS * 4 : T::U_STRIDE; }
+  static constexpr int pbytes_of(bool lead) { return (lead ? T::U_STRIDE : 0) + TILE_BYTES; }
   // 2*(NSU+NSP) mbarriers + an abort flag, padded to 128 bytes
-  static constexpr int bar_bytes(int nsu) { return ((16 * (nsu + T::NSP) + 16 + 127) / 128) * 128; }
-  // Classic design: the queue-feed ring holds halo planes z .. z+R+pf, and
-  // the per-point ring the tiles.
-  static constexpr int classic_smem(int pf) {
-    return bar_bytes(T::RZ + 1 + pf) + (T::RZ + 1 + pf) * T::U_STRIDE + T::NSP * TILE_BYTES + 128;
+  static constexpr int bar_bytes(int nsu, int nsp) { return ((16 * (nsu + nsp) + 16 + 127) / 128) * 128; }
+  static constexpr int smem_of(bool lead, int pf, int nsp) {
+    return bar_bytes(nsu_of(lead, pf), nsp) + nsu_of(lead, pf) * qstride_of(lead) + nsp * pbytes_of(lead) + 128;
   }
-  // Lead-plane design: the register queue is fed from a small ring of
-  // interior boxes of plane z+R, and the halo box of the centre plane is
-  // loaded again (from L2) with the per-point tiles, so the shared ring holds
-  // only the prefetch depth instead of R+1+PF halo planes.  Used from radius 7
-  // on, and wherever the classic design would not fit two CTAs per SM.
-  static constexpr bool LEAD = (NDIM == 3) && (R >= kLeadMinR || classic_smem(2) > kSmemTwoCtas);
+  static constexpr bool fits(bool lead, int pf, int nsp) { return smem_of(lead, pf, nsp) <= kSmemTwoCtas; }
+
+  // Lead-plane design from radius 7 on, and wherever the classic design would
+  // not fit two CTAs per SM.
+  static constexpr bool LEAD = (NDIM == 3) && (R >= kLeadMinR || !fits(false, 2, 3));
   // Deep variant (classic design, not the imaging condition): two CTAs per SM
   // with a 4-plane prefetch (3 where 4 would not fit two CTAs) and, up to
   // radius 5, output planes taken in pairs (half the register-queue moves),
-  // which the 96 registers per thread at two CTAs allow.  The imaging steps
-  // are HBM-bound and keep the 2-plane prefetch.
-  static constexpr int DEEP_PF = classic_smem(4) <= kSmemTwoCtas ? 4 : (classic_smem(3) <= kSmemTwoCtas ? 3 : 0);
+  // which the 96 registers per thread at two CTAs allow.
+  static constexpr int DEEP_PF = fits(false, 4, 3) ? 4 : (fits(false, 3, 3) ? 3 : 0);
   static constexpr bool DEEP = NDIM == 3 && !LEAD && !mode_is_grad(MODE) && DEEP_PF > 0;
-  static constexpr int PF = NDIM == 3 ? (DEEP ? DEEP_PF : 2) : 0;  // planes prefetched ahead
-  static constexpr int NSU = LEAD ? PF + 1 : T::RZ + 1 + PF;  // queue-feed ring stages
+  // The imaging steps are HBM-bound and keep a 2-plane prefetch; with 16-bit
+  // snapshots their per-plane stages are smaller, and a 3-plane prefetch with
+  // a 4-stage per-point ring keeps more bytes in flight where it fits.
+  static constexpr bool G16_DEEP =
+      NDIM == 3 && mode_is_grad(MODE) && mode_snap_fmt(MODE) != 0 && fits(LEAD, 3, 4);
+  static constexpr int PF = NDIM == 3 ? (DEEP ? DEEP_PF : (G16_DEEP ? 3 : 2)) : 0;  // planes prefetched ahead
+  static constexpr int NSP = NDIM == 3 ? (G16_DEEP ? 4 : 3) : 1;                    // per-point ring stages
+  static constexpr int NSU = nsu_of(LEAD, PF);                                       // queue-feed ring stages
   static constexpr int Q_BYTES = LEAD ? T::T_ELEMS * 4 : T::U_BYTES;
-  static constexpr int Q_STRIDE = LEAD ? T::T_ELEMS * 4 : T::U_STRIDE;
+  static constexpr int Q_STRIDE = qstride_of(LEAD);
   static constexpr int QU = (DEEP && R <= 5) ? 2 : 1;  // output planes per register-queue move
   // resident CTAs per SM asked of the register allocator (registers per
   // thread follow the warps per SM sub-partition: 3 CTAs of 9 warps leave 72,
@@ -132,12 +142,12 @@ struct StepLayout {
   static constexpr int G_OFF = CM_OFF + T::T_ELEMS * 4;
   static constexpr int S_OFF = G_OFF + T::T_ELEMS * 4;
   static constexpr int P_TX = (LEAD ? T::U_BYTES : 0) + TILE_BYTES;  // bytes landing per plane stage
-  static constexpr int P_BYTES = PREV_OFF + TILE_BYTES;                // stage spacing
+  static constexpr int P_BYTES = pbytes_of(LEAD);                      // stage spacing
   static_assert(P_BYTES % 128 == 0, "per-point stage must keep 128-byte alignment");
-  static constexpr int BAR_BYTES = bar_bytes(NSU);
+  static constexpr int BAR_BYTES = bar_bytes(NSU, NSP);
   static constexpr int U_OFF = BAR_BYTES;
   static constexpr int PST_OFF = U_OFF + NSU * Q_STRIDE;
-  static constexpr int SMEM = PST_OFF + T::NSP * P_BYTES + 128;  // + runtime 128-byte alignment
+  static constexpr int SMEM = PST_OFF + NSP * P_BYTES + 128;  // + runtime 128-byte alignment
 };
 
 // ---------------------------------------------------------------------------
