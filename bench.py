@@ -212,8 +212,8 @@ def measured_traffic(kind, points):
         with open(TRAFFIC_TABLE) as fh:
             for line in fh:
                 cells = [c.strip() for c in line.strip().strip("|").split("|")]
-                if len(cells) == 3 and cells[0] == kind and cells[2] == digest:
-                    return float(cells[1]) * points
+                if len(cells) >= 3 and cells[0] == kind and cells[-1] == digest:
+                    return float(cells[-2]) * points
     except OSError:
         pass
     return None
