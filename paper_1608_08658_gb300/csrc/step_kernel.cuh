@@ -87,6 +87,17 @@ struct IntC {
   static constexpr int value = V;
 };
 
+// Calls f(IntC<0>{}), f(IntC<1>{}), ... in order while they return true.
+template <typename F, int I, int N>
+__device__ __forceinline__ bool call_in_order(F& f, IntC<I>, IntC<N>) {
+  if constexpr (I == N) {
+    return true;
+  } else {
+    if (!f(IntC<I>{})) return false;
+    return call_in_order(f, IntC<I + 1>{}, IntC<N>{});
+  }
+}
+
 template <int R, int NDIM, int MODE, bool ISO>
 __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayout<R, NDIM, MODE, ISO>::MIN_BLOCKS))
     step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
@@ -242,9 +253,14 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
   // processed in groups of QU: before a group starting at output plane z,
   // q[0 .. 2RZ-1] hold planes z-RZ .. z+RZ-1; plane z+u+RZ of the group lands
   // in q[2RZ+u], and the queue moves down by QU after the group (by one after
-  // a single plane).
+  // a single plane).  With UR > 1 (QU = 1) a group of UR planes renames the
+  // queue instead of moving it: output plane u of the group reads the plane at
+  // offset i of its window from q[(u + i) % NQ], and after the group the queue
+  // is rotated once by UR (no move at all when UR = NQ).
   constexpr int QU = L::QU;
   constexpr int NQ = 2 * RZ + QU;
+  constexpr int UR = L::UR;
+  static_assert(UR == 1 || QU == 1, "renamed groups take one plane per queue slot");
   float4 q[NQ];
 #pragma unroll
   for (int i = 0; i < NQ; ++i) q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -282,19 +298,22 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
   int ring_un = (2 * RZ) % L::NSU, ring_ps = 0;
   uint32_t phase_un = ((2 * RZ) / L::NSU) & 1, phase_ps = 0;
 
-  // One output plane z = z0 + j, taking its queue entries at offset O.
-  auto plane = [&](auto oc) -> bool {
+  // One output plane z = z0 + j, taking its queue entries at offset O of a
+  // window renamed by PH (entry i at q[(PH + O + i) % NQ]).
+  auto plane = [&](auto oc, auto phc) -> bool {
     constexpr int O = decltype(oc)::value;
+    constexpr int PH = decltype(phc)::value;
+    auto qi = [](int i) { return (PH + O + i) % NQ; };
     const int un = ring_un, ps = ring_ps;
     const int uc = un >= RZ ? un - RZ : un + L::NSU - RZ;  // slot of the centre plane
     bool good = mbar_wait_bounded(&fullU[un], phase_un, abort_flag, kWaitLimitNs);
     if (!__all_sync(0xffffffffu, good)) return false;
-    q[O + 2 * RZ] = lds4(Ubase + un * (L::Q_STRIDE / 4) + qofs);
+    q[qi(2 * RZ)] = lds4(Ubase + un * (L::Q_STRIDE / 4) + qofs);
     if constexpr (L::LEAD) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&emptyU[un]);
     }
-    const float4 c = q[O + RZ];
+    const float4 c = q[qi(RZ)];
     if constexpr (L::LEAD) {
       // the centre halo box arrives with the per-point tiles
       good = mbar_wait_bounded(&fullP[ps], phase_ps, abort_flag, kWaitLimitNs);
@@ -316,8 +335,8 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
         float2 sa = __fadd2_rn(make_float2(ya.x, ya.y), make_float2(yb.x, yb.y));
         float2 sb = __fadd2_rn(make_float2(ya.z, ya.w), make_float2(yb.z, yb.w));
         if constexpr (RZ > 0) {
-          const float4 za = q[O + RZ - k];
-          const float4 zb = q[O + RZ + k];
+          const float4 za = q[qi(RZ - k)];
+          const float4 zb = q[qi(RZ + k)];
           sa = __fadd2_rn(sa, __fadd2_rn(make_float2(za.x, za.y), make_float2(zb.x, zb.y)));
           sb = __fadd2_rn(sb, __fadd2_rn(make_float2(za.z, za.w), make_float2(zb.z, zb.w)));
         }
@@ -334,8 +353,8 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
     } else {
 #pragma unroll
       for (int k = 1; k <= RZ; ++k) {
-        const float4 a = q[O + RZ - k];
-        const float4 b = q[O + RZ + k];
+        const float4 a = q[qi(RZ - k)];
+        const float4 b = q[qi(RZ + k)];
         tap2(la, 2, k - 1, make_float2(a.x, a.y), make_float2(b.x, b.y));
         tap2(lb, 2, k - 1, make_float2(a.z, a.w), make_float2(b.z, b.w));
       }
@@ -486,19 +505,37 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
   };
   if (ok && QU == 2) {
     while (j + 2 <= nP) {
-      ok = plane(IntC<0>{});
+      ok = plane(IntC<0>{}, IntC<0>{});
       if (!ok) break;
       advance();
-      ok = plane(IntC<QU - 1>{});
+      ok = plane(IntC<QU - 1>{}, IntC<0>{});
       if (!ok) break;
       advance();
 #pragma unroll
       for (int i = 0; i < 2 * RZ; ++i) q[i] = q[i + QU];
     }
   }
+  if constexpr (UR > 1) {
+    auto renamed = [&](auto phc) -> bool {
+      if (!plane(IntC<0>{}, phc)) return false;
+      advance();
+      return true;
+    };
+    while (ok && j + UR <= nP) {
+      ok = call_in_order(renamed, IntC<0>{}, IntC<UR>{});
+      if (!ok) break;
+      if constexpr (UR % NQ != 0) {
+        float4 t[NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) t[i] = q[(i + UR) % NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) q[i] = t[i];
+      }
+    }
+  }
   if (ok) {
     while (j < nP) {
-      ok = plane(IntC<0>{});
+      ok = plane(IntC<0>{}, IntC<0>{});
       if (!ok) break;
       advance();
 #pragma unroll

@@ -60,6 +60,12 @@ constexpr int kLeadMinR = 7;
 // radius 5-6, equal below).
 constexpr int kIsoMinR = 7;
 __host__ __device__ constexpr bool iso_kernel(int R, bool equal_spacing) { return equal_spacing && R >= kIsoMinR; }
+// Radius from which the register queue of the equal-spacing kernels is
+// renamed over groups of planes instead of moved after every plane, and the
+// planes per group (4: no spill at 128 registers; a full period of 2R+1
+// planes spills).
+constexpr int kRenameMinR = 7;
+constexpr int kRenameGroup = 4;
 
 // Shared memory of one SM and the part the driver keeps per resident CTA.
 constexpr int kSmemPerSm = 228 * 1024;
@@ -131,6 +137,13 @@ struct StepLayout {
   static constexpr int Q_BYTES = LEAD ? T::T_ELEMS * 4 : T::U_BYTES;
   static constexpr int Q_STRIDE = qstride_of(LEAD);
   static constexpr int QU = (DEEP && R <= 5) ? 2 : 1;  // output planes per register-queue move
+  // Output planes per renamed group (1 = the queue moves after every plane).
+  // From radius 7 the 2R moves per plane are a large part of the instruction
+  // stream and no register is left for QU = 2; renaming the 2R+1 slots over a
+  // group of UR planes and rotating once after it costs 2R+2 moves per group
+  // (order 16 forward step 0.934 -> 0.837 ms on 592^3).  The general-spacing
+  // kernels at these radii already spill under their register caps.
+  static constexpr int UR = (NDIM == 3 && ISO && R >= kRenameMinR) ? kRenameGroup : 1;
   // resident CTAs per SM asked of the register allocator (registers per
   // thread follow the warps per SM sub-partition: 3 CTAs of 9 warps leave 72,
   // 2 of 9 leave 96, 2 of 8 leave 128)
