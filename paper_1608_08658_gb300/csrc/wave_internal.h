@@ -60,11 +60,8 @@ constexpr int kLeadMinR = 7;
 // radius 5-6, equal below).
 constexpr int kIsoMinR = 7;
 __host__ __device__ constexpr bool iso_kernel(int R, bool equal_spacing) { return equal_spacing && R >= kIsoMinR; }
-// Radius from which the register queue of the equal-spacing kernels is
-// renamed over groups of planes instead of moved after every plane, and the
-// planes per group (4: no spill at 128 registers; a full period of 2R+1
-// planes spills).
-constexpr int kRenameMinR = 7;
+// Planes per renamed register-queue group where a full period of 2R+1 planes
+// would spill (see StepLayout::UR).
 constexpr int kRenameGroup = 4;
 
 // Shared memory of one SM and the part the driver keeps per resident CTA.
@@ -136,14 +133,27 @@ struct StepLayout {
   static constexpr int NSU = nsu_of(LEAD, PF);                                       // queue-feed ring stages
   static constexpr int Q_BYTES = LEAD ? T::T_ELEMS * 4 : T::U_BYTES;
   static constexpr int Q_STRIDE = qstride_of(LEAD);
-  static constexpr int QU = (DEEP && R <= 5) ? 2 : 1;  // output planes per register-queue move
-  // Output planes per renamed group (1 = the queue moves after every plane).
-  // From radius 7 the 2R moves per plane are a large part of the instruction
-  // stream and no register is left for QU = 2; renaming the 2R+1 slots over a
-  // group of UR planes and rotating once after it costs 2R+2 moves per group
-  // (order 16 forward step 0.934 -> 0.837 ms on 592^3).  The general-spacing
-  // kernels at these radii already spill under their register caps.
-  static constexpr int UR = (NDIM == 3 && ISO && R >= kRenameMinR) ? kRenameGroup : 1;
+  static constexpr int QU = (DEEP && R <= 2) ? 2 : 1;  // output planes per register-queue move
+  // Output planes per renamed group (1 = the queue moves after every plane):
+  // the 2R+1 queue slots are renamed over a group of UR planes and rotated
+  // once after it (2R+2 moves per group instead of 2R per plane); a group of
+  // a full period, 2R+1 planes, needs no rotation at all.  Chosen per kernel
+  // from measurements on 592^3 and the ptxas spill counts:
+  //  * full period for the deep forward / snapshot steps at radius 3-4 and the
+  //    FP32 imaging step at radius 4 (order 8 forward 0.545 -> 0.524 ms);
+  //  * groups of 4 for the other kernels up to radius 6 (order 12 forward
+  //    0.710 -> 0.667 ms, 16-bit imaging steps 4-6 % faster) and the
+  //    equal-spacing kernels from radius 7 (order 16 forward 0.934 -> 0.837 ms);
+  //  * none where a group spills under the register cap (imaging at radius 5,
+  //    16-bit snapshot, imaging and Born steps at radius 6, general spacing
+  //    from radius 7) and for the paired planes of the deep steps up to
+  //    radius 2 (no measurable difference there).
+  static constexpr int UR =
+      (NDIM != 3 || QU != 1) ? 1
+      : (R >= kLeadMinR) ? (ISO ? kRenameGroup : 1)
+      : ((R == 5 && mode_is_grad(MODE)) || (R == 6 && MODE >= MODE_SNAP_BF16)) ? 1
+      : ((DEEP && (R == 3 || R == 4)) || (R == 4 && MODE == MODE_GRAD_F32)) ? 2 * R + 1
+      : kRenameGroup;
   // resident CTAs per SM asked of the register allocator (registers per
   // thread follow the warps per SM sub-partition: 3 CTAs of 9 warps leave 72,
   // 2 of 9 leave 96, 2 of 8 leave 128)
