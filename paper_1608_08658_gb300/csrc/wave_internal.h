@@ -119,7 +119,7 @@ struct StepLayout {
   static constexpr bool LEAD = (NDIM == 3) && (R >= kLeadMinR || !fits(false, 2, 3));
   // Deep variant (classic design, not the imaging condition): two CTAs per SM
   // with a 4-plane prefetch (3 where 4 would not fit two CTAs) and, up to
-  // radius 5, output planes taken in pairs (half the register-queue moves),
+  // radius 2, output planes taken in pairs (half the register-queue moves),
   // which the 96 registers per thread at two CTAs allow.
   static constexpr int DEEP_PF = fits(false, 4, 3) ? 4 : (fits(false, 3, 3) ? 3 : 0);
   static constexpr bool DEEP = NDIM == 3 && !LEAD && !mode_is_grad(MODE) && DEEP_PF > 0;
@@ -128,8 +128,17 @@ struct StepLayout {
   // a 4-stage per-point ring keeps more bytes in flight where it fits.
   static constexpr bool G16_DEEP =
       NDIM == 3 && mode_is_grad(MODE) && mode_snap_fmt(MODE) != 0 && fits(LEAD, 3, 4);
-  static constexpr int PF = NDIM == 3 ? (DEEP ? DEEP_PF : (G16_DEEP ? 3 : 2)) : 0;  // planes prefetched ahead
-  static constexpr int NSP = NDIM == 3 ? (G16_DEEP ? 4 : 3) : 1;                    // per-point ring stages
+  // Lead-plane kernels from radius 7 (every mode): the deepest prefetch of 4
+  // planes (5 per-point stages) or 3 (4 stages) that fits two CTAs per SM.
+  // Their register queue and per-plane arithmetic leave the ring little slack:
+  // order 16 forward 0.838 -> 0.827 ms, snapshot 0.884 -> 0.860 ms, FP32
+  // imaging 0.982 -> 0.964 ms on 592^3.
+  static constexpr int LEAD_PF =
+      (NDIM == 3 && LEAD && R >= kLeadMinR) ? (fits(true, 4, 5) ? 4 : (fits(true, 3, 4) ? 3 : 0)) : 0;
+  static constexpr int PF =
+      NDIM == 3 ? (DEEP ? DEEP_PF : (LEAD_PF > 0 ? LEAD_PF : (G16_DEEP ? 3 : 2))) : 0;  // planes prefetched ahead
+  static constexpr int NSP =
+      NDIM == 3 ? (LEAD_PF > 0 ? LEAD_PF + 1 : (G16_DEEP ? 4 : 3)) : 1;  // per-point ring stages
   static constexpr int NSU = nsu_of(LEAD, PF);                                       // queue-feed ring stages
   static constexpr int Q_BYTES = LEAD ? T::T_ELEMS * 4 : T::U_BYTES;
   static constexpr int Q_STRIDE = qstride_of(LEAD);
