@@ -195,27 +195,39 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None, "samples": len(self.rows), "reasons": reasons}
 
 
-KERNEL_SOURCES = ("step_kernel.cuh", "ptx.cuh", "wave_internal.h")
-TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "step_kernel_r4_3d_336cube.md")
+KERNEL_SOURCES = ("step_kernel.cuh", "ptx.cuh")
+TRAFFIC_TABLES = [os.path.join(ROOT, "profiles", f) for f in
+                  ("step_kernel_r4_3d_336cube.md", "step_kernel_r8_3d_336cube.md")]
 
 
-def measured_traffic(kind, points):
-    """DRAM bytes per launch from the committed ncu summary, scaled to `points`;
-    None when the kernel sources changed since the counters were taken."""
+def kernel_key(space_order, ndim, kernel, equal_spacing):
+    """Identity of one compiled step kernel: its source files and its compile-time
+    configuration (wave_step_kernel_layout).  A counter taken on a kernel is valid
+    while the key is unchanged."""
     import hashlib
+    from paper_1608_08658_gb300 import wave
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_1608_08658_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    digest = h.hexdigest()[:16]
-    try:
-        with open(TRAFFIC_TABLE) as fh:
-            for line in fh:
-                cells = [c.strip() for c in line.strip().strip("|").split("|")]
-                if len(cells) >= 3 and cells[0] == kind and cells[-1] == digest:
-                    return float(cells[-2]) * points
-    except OSError:
-        pass
+    layout = wave.wave_step_kernel_layout(space_order, ndim, kernel, equal_spacing)
+    h.update(",".join(str(v) for v in layout.values()).encode())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(key, points):
+    """DRAM bytes per launch from the committed ncu summaries (bytes per point of
+    the kernel with this key), scaled to `points`; None when no summary holds a
+    counter of this exact kernel."""
+    for table in TRAFFIC_TABLES:
+        try:
+            with open(table) as fh:
+                for line in fh:
+                    cells = [c.strip() for c in line.strip().strip("|").split("|")]
+                    if len(cells) >= 3 and cells[-1] == key:
+                        return float(cells[-2]) * points
+        except OSError:
+            pass
     return None
 
 
@@ -386,8 +398,12 @@ def run_ours(args, rank, world, local_rank):
                           "bytes_per_point": bpp[k], "achieved_gbs": bpp[k] * npts / (avg * 1e-3) / 1e9}
     dom = max(kernels, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["launches"])
     ach = kernels[dom]["achieved_gbs"]
+    fmt = "bf16" if "bf16" in args.snap else ("fp16" if "fp16" in args.snap else "fp32")
+    dom_kernel = {"step": "plain", "step_snap": "snap_" + fmt, "step_grad": "grad_" + fmt}[dom]
+    key = kernel_key(so, len(w["shape"]), dom_kernel, len(set(w["spacing"])) == 1)
     roofline = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": measured_traffic(dom, npts) if so == 8 and not fmt16 else None, "kernel": dom, "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs copy test)"
+                "traffic": measured_traffic(key, npts), "kernel": dom, "kernel_key": key,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs copy test)"
                 if peak_kind == "measured" else "fallback 6.8 TB/s", "bytes_per_point": bpp[dom],
                 "points_per_launch": npts}
 

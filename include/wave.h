@@ -350,6 +350,30 @@ WAVE_API int wave_context_set_profiling(wave_context* ctx, int enable);
 WAVE_API int wave_context_kernel_stats(wave_context* ctx, int kind, int64_t* launches, double* total_ms);
 WAVE_API int wave_context_reset_stats(wave_context* ctx);
 
+/* Compile-time configuration of the stencil-step kernel that the library
+ * launches for one (space_order, ndim, kernel, equal_spacing), for profiling
+ * records: a measurement taken on a kernel stays valid while this list and the
+ * kernel's source are unchanged.  The paper has no counterpart (its code
+ * generator fixes such choices per problem, Sec. IV-B).  Host-only: no device
+ * work, usable without a GPU.
+ *   kernel: 0 plain step, 1/2/3 step storing an FP32/BF16/FP16 snapshot,
+ *           4/5/6 adjoint step with the imaging condition reading an
+ *           FP32/BF16/FP16 snapshot, 7 Born background step, 8 scattered step;
+ *   equal_spacing: nonzero when every axis has the same spacing (selects the
+ *           equal-spacing variant where one exists);
+ *   out:    receives up to n_out ints, in this order: radius, ndim, kernel,
+ *           equal-spacing variant used (0/1), x outputs per CTA, axis-1 outputs
+ *           per CTA, x halo, threads per CTA, CTAs per SM asked of the register
+ *           allocator, lead-plane design (0/1), planes prefetched, queue-feed
+ *           ring stages, per-point ring stages, output planes per queue move,
+ *           output planes per renamed queue group, dynamic shared memory bytes.
+ *   n_values: receives the number of values of the configuration (16); at
+ *           most n_out of them are written.
+ * Errors: INVALID_ARG (invalid order, ndim or kernel, NULL out or n_values,
+ * n_out < 1). */
+WAVE_API int wave_step_kernel_layout(int space_order, int ndim, int kernel, int equal_spacing, int* out, int n_out,
+                                     int* n_values);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,7 +6,8 @@ namespace wave {
 #define WAVE_DECLARE_RADIUS(RR)                                                                          \
   cudaError_t launch_step_r##RR(int ndim, int mode, const StepMaps& maps, const StepParams& p, dim3 grid, \
                                 cudaStream_t s);                                                        \
-  int step_smem_r##RR(int ndim, int mode, bool iso);
+  int step_smem_r##RR(int ndim, int mode, bool iso);                                                    \
+  int step_layout_r##RR(int ndim, int mode, bool iso, int* out);
 WAVE_DECLARE_RADIUS(1)
 WAVE_DECLARE_RADIUS(2)
 WAVE_DECLARE_RADIUS(3)
@@ -41,6 +42,20 @@ int step_smem_bytes(int R, int ndim, int mode, bool iso) {
     case 6: return step_smem_r6(ndim, mode, iso);
     case 7: return step_smem_r7(ndim, mode, iso);
     case 8: return step_smem_r8(ndim, mode, iso);
+    default: return -1;
+  }
+}
+
+int step_layout(int R, int ndim, int mode, bool iso, int* out) {
+  switch (R) {
+    case 1: return step_layout_r1(ndim, mode, iso, out);
+    case 2: return step_layout_r2(ndim, mode, iso, out);
+    case 3: return step_layout_r3(ndim, mode, iso, out);
+    case 4: return step_layout_r4(ndim, mode, iso, out);
+    case 5: return step_layout_r5(ndim, mode, iso, out);
+    case 6: return step_layout_r6(ndim, mode, iso, out);
+    case 7: return step_layout_r7(ndim, mode, iso, out);
+    case 8: return step_layout_r8(ndim, mode, iso, out);
     default: return -1;
   }
 }

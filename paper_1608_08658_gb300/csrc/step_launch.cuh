@@ -71,6 +71,35 @@ static int smem_modes(int mode) {
   }
 }
 
+// Compile-time configuration of one step kernel, in the order documented for
+// wave_step_kernel_layout; returns the number of values.
+template <int R, int NDIM, int MODE, bool ISO>
+static int layout_one(int* out) {
+  using T = StepTraits<R, NDIM, ISO>;
+  using L = StepLayout<R, NDIM, MODE, ISO>;
+  const int v[] = {R, NDIM, MODE, ISO ? 1 : 0, T::BX, T::BY, T::HX, T::NTHREADS, L::MIN_BLOCKS, L::LEAD ? 1 : 0,
+                   L::PF, L::NSU, L::NSP, L::QU, L::UR, L::SMEM};
+  constexpr int n = sizeof(v) / sizeof(v[0]);
+  for (int i = 0; i < n; ++i) out[i] = v[i];
+  return n;
+}
+
+template <int R, int NDIM, bool ISO>
+static int layout_modes(int mode, int* out) {
+  switch (mode) {
+    case MODE_PLAIN: return layout_one<R, NDIM, MODE_PLAIN, ISO>(out);
+    case MODE_SNAP_F32: return layout_one<R, NDIM, MODE_SNAP_F32, ISO>(out);
+    case MODE_SNAP_BF16: return layout_one<R, NDIM, MODE_SNAP_BF16, ISO>(out);
+    case MODE_SNAP_F16: return layout_one<R, NDIM, MODE_SNAP_F16, ISO>(out);
+    case MODE_GRAD_F32: return layout_one<R, NDIM, MODE_GRAD_F32, ISO>(out);
+    case MODE_GRAD_BF16: return layout_one<R, NDIM, MODE_GRAD_BF16, ISO>(out);
+    case MODE_GRAD_F16: return layout_one<R, NDIM, MODE_GRAD_F16, ISO>(out);
+    case MODE_BORN_SRC: return layout_one<R, NDIM, MODE_BORN_SRC, ISO>(out);
+    case MODE_SRC: return layout_one<R, NDIM, MODE_SRC, ISO>(out);
+    default: return -1;
+  }
+}
+
 }  // namespace wave
 
 // Defines the per-radius entry points used by step_dispatch.cu.
@@ -84,5 +113,10 @@ static int smem_modes(int mode) {
     if (iso_kernel(RR, iso))                                                                            \
       return ndim == 3 ? smem_modes<RR, 3, true>(mode) : smem_modes<RR, 2, true>(mode);                 \
     return ndim == 3 ? smem_modes<RR, 3, false>(mode) : smem_modes<RR, 2, false>(mode);                 \
+  }                                                                                                     \
+  int step_layout_r##RR(int ndim, int mode, bool iso, int* out) {                                       \
+    if (iso_kernel(RR, iso))                                                                            \
+      return ndim == 3 ? layout_modes<RR, 3, true>(mode, out) : layout_modes<RR, 2, true>(mode, out);   \
+    return ndim == 3 ? layout_modes<RR, 3, false>(mode, out) : layout_modes<RR, 2, false>(mode, out);   \
   }                                                                                                     \
   }

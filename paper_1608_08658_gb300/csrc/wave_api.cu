@@ -1755,6 +1755,19 @@ int wave_ricker(float* q_out, int nt, float dt, float f0, float t0) {
   return WAVE_OK;
 }
 
+int wave_step_kernel_layout(int space_order, int ndim, int kernel, int equal_spacing, int* out, int n_out,
+                            int* n_values) {
+  if (!valid_order(space_order) || (ndim != 2 && ndim != 3) || kernel < 0 || kernel >= MODE_COUNT || !out ||
+      n_out < 1 || !n_values)
+    return WAVE_ERR_INVALID_ARG;
+  int v[16];
+  const int n = step_layout(space_order / 2, ndim, kernel, equal_spacing != 0, v);
+  if (n < 0 || n > 16) return WAVE_ERR_INVALID_ARG;
+  for (int i = 0; i < n && i < n_out; ++i) out[i] = v[i];
+  *n_values = n;
+  return WAVE_OK;
+}
+
 int wave_context_set_profiling(wave_context* ctx, int enable) {
   if (!ctx) return WAVE_ERR_INVALID_ARG;
   ctx->profiling = enable != 0;

@@ -227,6 +227,9 @@ cudaError_t launch_step(int R, int ndim, int mode, const StepMaps& maps, const S
                         dim3 grid, cudaStream_t stream);
 // Tile geometry of StepTraits<R, NDIM, iso> for the host (maps and grid).
 int step_smem_bytes(int R, int ndim, int mode, bool iso);
+// Compile-time configuration of the step kernel launched for (R, ndim, mode,
+// equal spacing); returns the number of values written to out (at most 16).
+int step_layout(int R, int ndim, int mode, bool iso, int* out);
 int step_bx();
 int step_by(int R, int ndim, bool iso);
 int step_hx(int R);

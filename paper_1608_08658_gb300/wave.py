@@ -86,6 +86,9 @@ _SIGS = {
     "wave_context_kernel_stats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                                  ctypes.POINTER(ctypes.c_double)]),
     "wave_context_reset_stats": (ctypes.c_int, [_P]),
+    "wave_step_kernel_layout": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int)]),
     "wave_objective_noalloc": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), _P]),
     "wave_session_footprint": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int,
                                               ctypes.POINTER(ctypes.c_size_t)]),
@@ -502,6 +505,26 @@ def wave_dt_max(spacing, space_order, v_max):
     if v < 0:
         raise WaveError(WAVE_ERR_INVALID_ARG, "bad arguments to wave_dt_max")
     return v
+
+
+STEP_KERNELS = {"plain": 0, "snap_fp32": 1, "snap_bf16": 2, "snap_fp16": 3, "grad_fp32": 4, "grad_bf16": 5,
+                "grad_fp16": 6, "born_background": 7, "scattered": 8}
+STEP_LAYOUT_FIELDS = ("radius", "ndim", "kernel", "equal_spacing_variant", "bx", "by", "hx", "threads",
+                      "ctas_per_sm", "lead_plane", "prefetch", "queue_stages", "point_stages", "planes_per_move",
+                      "planes_per_renamed_group", "smem_bytes")
+
+
+def wave_step_kernel_layout(space_order, ndim, kernel, equal_spacing):
+    """Compile-time configuration (dict) of the step kernel launched for these
+    arguments; host-only (no GPU needed).  `kernel` is a STEP_KERNELS name or code."""
+    k = STEP_KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
+    buf = (ctypes.c_int * 16)()
+    n = ctypes.c_int()
+    rc = lib().wave_step_kernel_layout(int(space_order), int(ndim), k, int(bool(equal_spacing)), buf, 16,
+                                       ctypes.byref(n))
+    if rc != WAVE_OK:
+        raise WaveError(rc, "bad arguments to wave_step_kernel_layout")
+    return dict(zip(STEP_LAYOUT_FIELDS, list(buf)[:n.value]))
 
 
 def wave_ricker(nt, dt, f0, t0=None, out=None):

@@ -78,3 +78,36 @@ def test_context_without_gpu_reports_error(lib):
     assert rc in (wave.WAVE_ERR_CUDA, wave.WAVE_ERR_NOT_SUPPORTED)
     assert not h.value
     assert lib.wave_context_destroy(None) == 0
+
+
+def test_step_kernel_layout(lib):
+    """Host-only layout query: the tile of every step kernel covers whole 16-byte
+    quads, two CTAs fit one SM's shared memory and register file, and the
+    register-queue settings are consistent (paired planes and renamed groups
+    exclude each other)."""
+    smem_two_ctas = 228 * 1024 // 2 - 1024
+    for so in range(2, 17, 2):
+        R = so // 2
+        for ndim in (2, 3):
+            for kernel in range(9):
+                for eq in (0, 1):
+                    L = wave.wave_step_kernel_layout(so, ndim, kernel, eq)
+                    assert (L["radius"], L["ndim"], L["kernel"]) == (R, ndim, kernel)
+                    assert L["equal_spacing_variant"] == int(bool(eq) and R >= 7)
+                    assert L["bx"] % 4 == 0 and L["hx"] % 4 == 0 and L["hx"] >= min(R, 8) - 4
+                    assert L["threads"] == (L["by"] // 2 + 1) * 32
+                    assert L["smem_bytes"] <= smem_two_ctas
+                    assert L["ctas_per_sm"] * L["threads"] <= 2048
+                    if ndim == 2:
+                        assert L["prefetch"] == 0 and L["planes_per_renamed_group"] == 1
+                        continue
+                    assert L["planes_per_move"] == 1 or L["planes_per_renamed_group"] == 1
+                    assert L["planes_per_renamed_group"] >= 1
+                    q = L["queue_stages"]
+                    assert q == (L["prefetch"] + 1 if L["lead_plane"] else R + 1 + L["prefetch"])
+    with pytest.raises(wave.WaveError):
+        wave.wave_step_kernel_layout(7, 3, 0, 1)
+    with pytest.raises(wave.WaveError):
+        wave.wave_step_kernel_layout(8, 3, 9, 1)
+    with pytest.raises(wave.WaveError):
+        wave.wave_step_kernel_layout(8, 4, 0, 1)
