@@ -26,7 +26,8 @@ def _dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-@pytest.mark.parametrize("case", ["3d8", "2d4", "3d12", "3d16", "3d8iso", "3d16iso"])
+@pytest.mark.parametrize("case", ["3d2", "3d4", "3d6", "3d8", "3d10", "2d4", "3d12", "3d14", "3d16", "3d8iso",
+                                  "3d14iso", "3d16iso"])
 def test_born_matches_oracle(ctx, case):
     so = int(case[2:].replace("iso", ""))
     h = (10.0, 10.0, 10.0) if case.endswith("iso") else (10.0, 12.0, 9.0)
