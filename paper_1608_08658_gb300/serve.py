@@ -94,22 +94,29 @@ class ShotServer:
         free_slots = list(range(len(self.streams)))
         active = []
         stats = ServeStats()
+        head = None  # (request id, materialised problem, footprint) of the first waiting request
         t0 = time.perf_counter()
         while pending or waiting or active:
             now = time.perf_counter() - t0
             while pending and pending[0][1] <= now:
                 waiting.append(pending.popleft())
             progressed = False
-            # admission in arrival order by slot and footprint
+            # admission in arrival order by slot and footprint; a request that
+            # waits for memory is materialised once, not at every poll
             while waiting and free_slots:
                 req, arr = waiting[0]
-                geom, m, src, q, rec, dt = problem(req, self.device)
-                fp = wave.wave_session_footprint(self.ctx, geom, src, rec, req["nt"], req["so"])
+                if head is None or head[0] != req["id"]:
+                    prob = problem(req, self.device)
+                    geom, src, rec = prob[0], prob[2], prob[4]
+                    head = (req["id"], prob, wave.wave_session_footprint(self.ctx, geom, src, rec, req["nt"],
+                                                                         req["so"]))
+                _, (geom, m, src, q, rec, dt), fp = head
                 if self.budget and fp > self.ctx.budget_free():
                     if not active:
                         raise RuntimeError("request %d needs %d bytes, more than the whole budget" % (req["id"], fp))
                     break
                 waiting.popleft()
+                head = None
                 slot = free_slots.pop()
                 stream = self.streams[slot]
                 sess = wave.Session(self.ctx, geom, m, src, q, rec, dt, req["nt"], req["so"],
