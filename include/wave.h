@@ -149,6 +149,28 @@ WAVE_API int wave_context_set_checkpoint_interval(wave_context* ctx, int steps);
  * number of checkpointed segments (0 = full storage). */
 WAVE_API int wave_context_storage_plan(const wave_context* ctx, int* levels, int* parts, int* segments);
 
+/* The storage plan wave_gradient chooses for the forward wavefield of Eq. 3
+ * (the snapshots the imaging condition reads), for given sizes; host-only, no
+ * device work, usable without a GPU.  A buffer of `levels` snapshot levels
+ * holds the last levels of the forward sweep; the earlier levels are covered by
+ * `segments` checkpointed segments of parts * levels levels, each starting at
+ * an exact FP32 checkpoint of two wavefields and rebuilt part by part in the
+ * reverse sweep (segments = 0: every level stored).
+ *   nt:          time levels (>= 2);
+ *   level_bytes: bytes of one stored snapshot level (> 0);
+ *   field_bytes: bytes of one FP32 wavefield (a checkpoint holds two);
+ *   avail_bytes: memory for the buffer and the checkpoints;
+ *   checkpoint:  0 = store every level (full storage), else plan checkpoints;
+ *   checkpoint_interval: > 0 fixes the buffer at that many levels (one part
+ *                per segment), 0 = the smallest parts per segment (1, 2, 4
+ *                .. 64) for which a buffer fits, with the largest such buffer.
+ * levels, parts, segments may be NULL.
+ * Errors: INVALID_ARG (nt < 2, level_bytes = 0, checkpoint_interval < 0);
+ * OUT_OF_MEMORY (with checkpoint and no fixed interval, when not even a
+ * one-level buffer with its checkpoints fits). */
+WAVE_API int wave_storage_plan_for(int nt, size_t level_bytes, size_t field_bytes, size_t avail_bytes, int checkpoint,
+                                   int checkpoint_interval, int* levels, int* parts, int* segments);
+
 /* Text of a status code, and the last error message of a context. */
 WAVE_API const char* wave_error_string(int status);
 WAVE_API const char* wave_last_error(const wave_context* ctx);

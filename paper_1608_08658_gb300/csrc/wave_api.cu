@@ -1159,6 +1159,42 @@ struct StoragePlan {
   int nseg = 0;  // checkpointed segments covering levels [0, T0)
 };
 
+// The sizing rule alone: lb bytes per buffer level, fb bytes per FP32 field
+// (a checkpoint holds two), avail bytes for buffer and checkpoints.  Full
+// storage unless ckpt; with ckpt, a fixed buffer of ckpt_interval levels if
+// that is positive, else the smallest k (1, 2, 4 .. 64) for which some buffer
+// fits, with the largest buffer that fits for that k.
+int plan_levels(int nt, size_t lb, size_t fb, size_t avail, bool ckpt, int ckpt_interval, StoragePlan* plan) {
+  int F = nt - 1, k = 1;
+  if (ckpt) {
+    if (ckpt_interval > 0) {
+      F = std::min(ckpt_interval, nt - 1);
+    } else {
+      auto fits = [&](int FF, int kk) {
+        const int T0 = nt - FF;
+        const size_t nseg = static_cast<size_t>((T0 + kk * FF - 1) / (kk * FF));
+        return static_cast<size_t>(FF) * lb + nseg * 2 * fb <= avail;
+      };
+      const int Fcap = static_cast<int>(std::min<size_t>(avail / lb, static_cast<size_t>(nt - 1)));
+      F = 0;
+      for (k = 1; k <= 64 && F == 0; k *= 2)
+        for (int FF = Fcap; FF >= 1; --FF)
+          if (fits(FF, k)) {
+            F = FF;
+            break;
+          }
+      k = F ? k / 2 : 1;
+      if (F == 0) return WAVE_ERR_OUT_OF_MEMORY;
+    }
+  }
+  plan->F = F;
+  plan->k = k;
+  plan->S = k * F;
+  plan->T0 = nt - F;
+  plan->nseg = plan->T0 > 1 ? (plan->T0 + plan->S - 1) / plan->S : 0;
+  return WAVE_OK;
+}
+
 int plan_storage(wave_context* ctx, Prob& P, int mode, StoragePlan* plan) {
   if (mode < WAVE_SNAP_FULL_FP32 || mode > WAVE_SNAP_AUTO) return fail(ctx, WAVE_ERR_INVALID_ARG, "bad snap_mode %d", mode);
   const int nt = P.nt;
@@ -1191,36 +1227,9 @@ int plan_storage(wave_context* ctx, Prob& P, int mode, StoragePlan* plan) {
     case WAVE_SNAP_CHECKPOINT_FP16: f = 2; ckpt = true; break;
     case WAVE_SNAP_AUTO: f = 0; ckpt = level_bytes(0) * static_cast<size_t>(nt - 1) > avail; break;
   }
-  const size_t lb = level_bytes(f);
-  int F = nt - 1, k = 1;
-  if (ckpt) {
-    if (ctx->ckpt_interval > 0) {
-      F = std::min(ctx->ckpt_interval, nt - 1);
-    } else {
-      // smallest k for which some buffer size fits; the largest such buffer
-      auto fits = [&](int FF, int kk) {
-        const int T0 = nt - FF;
-        const size_t nseg = static_cast<size_t>((T0 + kk * FF - 1) / (kk * FF));
-        return static_cast<size_t>(FF) * lb + nseg * 2 * fb <= avail;
-      };
-      const int Fcap = static_cast<int>(std::min<size_t>(avail / lb, static_cast<size_t>(nt - 1)));
-      F = 0;
-      for (k = 1; k <= 64 && F == 0; k *= 2)
-        for (int FF = Fcap; FF >= 1; --FF)
-          if (fits(FF, k)) {
-            F = FF;
-            break;
-          }
-      k = F ? k / 2 : 1;
-      if (F == 0) return fail(ctx, WAVE_ERR_OUT_OF_MEMORY, "the forward wavefield storage does not fit in memory");
-    }
-  }
   plan->fmt = f;
-  plan->F = F;
-  plan->k = k;
-  plan->S = k * F;
-  plan->T0 = nt - F;
-  plan->nseg = plan->T0 > 1 ? (plan->T0 + plan->S - 1) / plan->S : 0;
+  if (plan_levels(nt, level_bytes(f), fb, avail, ckpt, ctx->ckpt_interval, plan) != WAVE_OK)
+    return fail(ctx, WAVE_ERR_OUT_OF_MEMORY, "the forward wavefield storage does not fit in memory");
   return WAVE_OK;
 }
 
@@ -1900,6 +1909,18 @@ int wave_session_destroy(wave_session* S) {
   sess_free(S);
   cudaGetLastError();
   delete S;
+  return WAVE_OK;
+}
+
+int wave_storage_plan_for(int nt, size_t level_bytes, size_t field_bytes, size_t avail_bytes, int checkpoint,
+                          int checkpoint_interval, int* levels, int* parts, int* segments) {
+  if (nt < 2 || level_bytes == 0 || checkpoint_interval < 0) return WAVE_ERR_INVALID_ARG;
+  StoragePlan plan;
+  const int rc = plan_levels(nt, level_bytes, field_bytes, avail_bytes, checkpoint != 0, checkpoint_interval, &plan);
+  if (rc != WAVE_OK) return rc;
+  if (levels) *levels = plan.F;
+  if (parts) *parts = plan.k;
+  if (segments) *segments = plan.nseg;
   return WAVE_OK;
 }
 

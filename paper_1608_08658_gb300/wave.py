@@ -101,6 +101,9 @@ _SIGS = {
     "wave_context_budget_free": (ctypes.c_size_t, [_P]),
     "wave_context_storage_plan": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                                  ctypes.POINTER(ctypes.c_int)]),
+    "wave_storage_plan_for": (ctypes.c_int, [ctypes.c_int, ctypes.c_size_t, ctypes.c_size_t, ctypes.c_size_t,
+                                             ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
 }
 
 _lib = None
@@ -505,6 +508,18 @@ def wave_dt_max(spacing, space_order, v_max):
     if v < 0:
         raise WaveError(WAVE_ERR_INVALID_ARG, "bad arguments to wave_dt_max")
     return v
+
+
+def wave_storage_plan_for(nt, level_bytes, field_bytes, avail_bytes, checkpoint=True, checkpoint_interval=0):
+    """(buffer levels, parts per segment, checkpointed segments) that the
+    gradient's storage planner chooses for these sizes; host-only."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    rc = lib().wave_storage_plan_for(int(nt), int(level_bytes), int(field_bytes), int(avail_bytes),
+                                     int(bool(checkpoint)), int(checkpoint_interval), ctypes.byref(a),
+                                     ctypes.byref(b), ctypes.byref(c))
+    if rc != WAVE_OK:
+        raise WaveError(rc, wave_error_string(rc))
+    return a.value, b.value, c.value
 
 
 STEP_KERNELS = {"plain": 0, "snap_fp32": 1, "snap_bf16": 2, "snap_fp16": 3, "grad_fp32": 4, "grad_bf16": 5,
