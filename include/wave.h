@@ -311,6 +311,22 @@ WAVE_API int wave_born(wave_context* ctx, const wave_geometry* geom, const float
  * w_j = 2 (-1)^{j+1} (R!)^2 / (j^2 (R-j)! (R+j)!)).  w_out holds R+1 doubles. */
 WAVE_API int wave_fd_weights(int space_order, double* w_out);
 
+/* Sparse-point interpolation operator P of a point set (Sec. IV; P_s and P_r
+ * of the discretisation above), read back from the structure the library
+ * builds to inject at and sample these points; host-only, no device work,
+ * usable without a GPU.
+ *   geom: as for wave_forward; pts: coordinates in HOST memory;
+ *   index_out: pts->n * 2^ndim int64, the computational-grid points of each
+ *     point's cell as linear indices of the dense computational grid, x
+ *     fastest: (iz * n_y + iy) * n_x + ix in 3D, iz * n_x + ix in 2D
+ *     (n_d = N_d + 2 nbl);
+ *   weight_out: pts->n * 2^ndim float32 weights; entry c of a point is the
+ *     cell corner whose axis-a index is the upper one when bit a of c is set.
+ * Errors: INVALID_ARG (NULL pointer, bad geometry, n < 0 or n > 2^28);
+ * POINT_OUTSIDE (a point outside the physical domain). */
+WAVE_API int wave_interpolation_operator(const wave_geometry* geom, const wave_points* pts, int64_t* index_out,
+                                         float* weight_out);
+
 /* Leapfrog stability limit dt_max = 2 / (v_max sqrt(sum_d (sum_j |w_j|)/h_d^2))
  * for the undamped scheme; returns a negative value on invalid input. */
 WAVE_API double wave_dt_max(int ndim, const double* spacing, int space_order, double v_max);

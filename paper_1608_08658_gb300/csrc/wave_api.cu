@@ -460,7 +460,7 @@ int prepare(wave_context* ctx, const wave_geometry* geom, float dt, int nt, int 
   sp.inv_dt2 = static_cast<float>(1.0 / (double(dt) * dt));
   sp.slabs_x = P->slabs_x;
   sp.slabs_y = P->slabs_y;
-  sp.status = ctx->d_status;
+  sp.status = ctx ? ctx->d_status : nullptr;  // no context: host-only queries
   // grid: x tiles, axis-1 tiles, chunks of the streamed axis
   const int tx = (g.NX + step_bx() - 1) / step_bx();
   const int ty = (g.NY + step_by(P->R, nd, sp.iso != 0) - 1) / step_by(P->R, nd, sp.iso != 0);
@@ -1909,6 +1909,37 @@ int wave_session_destroy(wave_session* S) {
   sess_free(S);
   cudaGetLastError();
   delete S;
+  return WAVE_OK;
+}
+
+int wave_interpolation_operator(const wave_geometry* geom, const wave_points* pts, int64_t* index_out,
+                                float* weight_out) {
+  if (!geom || !pts || pts->n < 0 || pts->n > (1LL << 28) || (pts->n > 0 && (!pts->coords || !index_out || !weight_out)))
+    return WAVE_ERR_INVALID_ARG;
+  Prob P;
+  // the time step and order do not enter the interpolation
+  TRY(prepare(nullptr, geom, 1.0f, 2, 2, &P));
+  const int nd = P.ndim, C = 1 << nd;
+  const long long n = pts->n;
+  std::vector<float> c(pts->coords, pts->coords + n * nd);
+  PointsHost H;
+  TRY(build_points_from(nullptr, P, c, 0, &H));
+  // read the operator back from the injection structure: rows are cells in
+  // increasing order, so each point's entries arrive in corner order
+  std::vector<int> filled(static_cast<size_t>(n), 0);
+  const long long pitch = P.g.pitch, NX = P.g.NX, NY = P.g.NY;
+  for (size_t r = 0; r + 1 < H.rowptr.size(); ++r) {
+    const long long cell = H.cells[r];
+    const long long x = cell % pitch, y = (cell / pitch) % NY, z = cell / (pitch * NY);
+    const long long dense = (z * NY + y) * NX + x;
+    for (int k = H.rowptr[r]; k < H.rowptr[r + 1]; ++k) {
+      const int p = H.pidx[k];
+      if (filled[p] >= C) return WAVE_ERR_INVALID_ARG;
+      index_out[static_cast<long long>(p) * C + filled[p]] = dense;
+      weight_out[static_cast<long long>(p) * C + filled[p]] = H.wts[k];
+      ++filled[p];
+    }
+  }
   return WAVE_OK;
 }
 

@@ -80,6 +80,7 @@ _SIGS = {
                                            ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_int, _P]),
     "wave_born": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, ctypes.c_int, _P]),
     "wave_fd_weights": (ctypes.c_int, [ctypes.c_int, _P]),
+    "wave_interpolation_operator": (ctypes.c_int, [_P, _P, _P, _P]),
     "wave_dt_max": (ctypes.c_double, [ctypes.c_int, _P, ctypes.c_int, ctypes.c_double]),
     "wave_ricker": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_float, ctypes.c_float, ctypes.c_float]),
     "wave_context_set_profiling": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -500,6 +501,23 @@ def wave_fd_weights(space_order):
     if rc != WAVE_OK:
         raise WaveError(rc, "bad space order %r" % (space_order,))
     return w
+
+
+def wave_interpolation_operator(geom, coords):
+    """Sparse-point interpolation operator of a point set as the library builds
+    it: (index, weight), each (n, 2^ndim), with dense computational-grid
+    indices (x fastest); host-only."""
+    c = np.ascontiguousarray(np.asarray(coords, dtype=np.float32).reshape(-1, geom.ndim))
+    n, C = c.shape[0], 1 << geom.ndim
+    idx = np.zeros((n, C), dtype=np.int64)
+    wts = np.zeros((n, C), dtype=np.float32)
+    g = geom.to_c()
+    pts = c_points(n, c.ctypes.data if n else None)
+    rc = lib().wave_interpolation_operator(ctypes.byref(g), ctypes.byref(pts), idx.ctypes.data if n else None,
+                                           wts.ctypes.data if n else None)
+    if rc != WAVE_OK:
+        raise WaveError(rc, wave_error_string(rc))
+    return idx, wts
 
 
 def wave_dt_max(spacing, space_order, v_max):
