@@ -1,0 +1,64 @@
+"""Compile-time resource guard for the step kernels of the benchmark
+workloads (no GPU needed): ptxas must place the order-8 kernels (every
+epilogue mode, 3D) and the equal-spacing order-16 forward step in their
+register caps without spilling, since a spill in these loops costs several
+per cent of HBM throughput.  Uses only what ptxas prints (-Xptxas -v)."""
+
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_1608_08658_gb300 import build as libbuild
+
+CSRC = libbuild.CSRC
+
+
+def _ptxas_report(radius):
+    nvcc = libbuild.nvcc()
+    src = os.path.join(CSRC, "step_r%d.cu" % radius)
+    with tempfile.TemporaryDirectory() as d:
+        cmd = [nvcc] + libbuild.ARCH + ["-O3", "-std=c++17", "--expt-relaxed-constexpr", "-Xptxas", "-v",
+                                        "-I", os.path.join(libbuild.ROOT, "include"), "-I", CSRC, "-c", src,
+                                        "-o", os.path.join(d, "k.o")]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out, cur, spill = {}, None, (0, 0)
+    for line in r.stderr.splitlines():
+        m = re.search(r"Compiling entry function .*step_kernelILi(\d+)ELi(\d+)ELi(\d+)ELb(\d)E", line)
+        if m:
+            cur, spill = tuple(int(x) for x in m.groups()), (0, 0)
+            continue
+        m = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", line)
+        if m and cur:
+            spill = (int(m.group(1)), int(m.group(2)))
+        m = re.search(r"Used (\d+) registers", line)
+        if m and cur:
+            out[cur] = (int(m.group(1)), spill)
+            cur = None
+    return out
+
+
+@pytest.fixture(scope="module")
+def have_nvcc():
+    try:
+        libbuild.nvcc()
+    except RuntimeError:
+        pytest.skip("nvcc not available")
+
+
+def test_order8_kernels_do_not_spill(have_nvcc):
+    rep = _ptxas_report(4)
+    k3 = {k: v for k, v in rep.items() if k[1] == 3}
+    assert len(k3) == 9, sorted(rep)
+    for (R, nd, mode, iso), (regs, spill) in k3.items():
+        assert spill == (0, 0), ((R, nd, mode, iso), spill)
+        assert regs <= 96, ((R, nd, mode, iso), regs)
+
+
+def test_order16_forward_step_does_not_spill(have_nvcc):
+    rep = _ptxas_report(8)
+    regs, spill = rep[(8, 3, 0, 1)]
+    assert spill == (0, 0) and regs <= 128
