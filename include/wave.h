@@ -144,6 +144,18 @@ WAVE_API int wave_context_trim(wave_context* ctx);
  * budget (default). */
 WAVE_API int wave_context_set_checkpoint_interval(wave_context* ctx, int steps);
 
+/* Limit, in nanoseconds, of each bounded wait by which a stencil-step kernel
+ * waits for its tile loads or for its own consumer warps (failure detection;
+ * the paper has no counterpart).  A kernel whose wait runs out records a
+ * timeout in the context's device status word, lets every copy it has issued
+ * land (those drain waits keep the default limit, so no CTA exits with a copy
+ * in flight) and returns; the call then returns WAVE_ERR_TIMEOUT and the
+ * context stays usable.  ns = 0 restores the default of 10 s.  A very small
+ * limit makes ordinary waits for data run out; it exists so that tests can
+ * exercise the timeout path without a fault or a hang.  Sessions take the
+ * limit in force when they are created.  Errors: INVALID_ARG (ctx NULL). */
+WAVE_API int wave_context_set_wait_limit_ns(wave_context* ctx, uint64_t ns);
+
 /* Storage plan of the context's last wave_gradient / wave_jacobian_adjoint
  * call: snapshot buffer levels F, parts per checkpointed segment k, and the
  * number of checkpointed segments (0 = full storage). */

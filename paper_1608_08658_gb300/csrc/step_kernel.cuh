@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
       bool ok = true;
       for (int s = 0; s < nU; ++s) {
         const int slot = s % L::NSU;
-        if (s >= L::NSU) ok = mbar_wait_bounded(&emptyU[slot], ((s / L::NSU) - 1) & 1, abort_flag, kWaitLimitNs);
+        if (s >= L::NSU) ok = mbar_wait_bounded(&emptyU[slot], ((s / L::NSU) - 1) & 1, abort_flag, p.wait_ns);
         if (!ok) break;
         mbar_arrive_expect_tx(&fullU[slot], L::Q_BYTES);
         if constexpr (L::LEAD)
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
         if (s >= 2 * RZ) {
           const int j = s - 2 * RZ;
           const int ps = j % L::NSP;
-          if (j >= L::NSP) ok = mbar_wait_bounded(&emptyP[ps], ((j / L::NSP) - 1) & 1, abort_flag, kWaitLimitNs);
+          if (j >= L::NSP) ok = mbar_wait_bounded(&emptyP[ps], ((j / L::NSP) - 1) & 1, abort_flag, p.wait_ns);
           if (!ok) break;
           unsigned char* pd = Pbase + ps * L::P_BYTES;
           mbar_arrive_expect_tx(&fullP[ps], L::P_TX);
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
 #pragma unroll
   for (int s = 0; s < 2 * RZ; ++s) {
     const int slot = s % L::NSU;
-    ok = mbar_wait_bounded(&fullU[slot], (s / L::NSU) & 1, abort_flag, kWaitLimitNs);
+    ok = mbar_wait_bounded(&fullU[slot], (s / L::NSU) & 1, abort_flag, p.wait_ns);
     ok = __all_sync(0xffffffffu, ok);
     if (!ok) break;
     q[s] = lds4(Ubase + slot * (L::Q_STRIDE / 4) + qofs);
@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
     auto qi = [](int i) { return (PH + O + i) % NQ; };
     const int un = ring_un, ps = ring_ps;
     const int uc = un >= RZ ? un - RZ : un + L::NSU - RZ;  // slot of the centre plane
-    bool good = mbar_wait_bounded(&fullU[un], phase_un, abort_flag, kWaitLimitNs);
+    bool good = mbar_wait_bounded(&fullU[un], phase_un, abort_flag, p.wait_ns);
     if (!__all_sync(0xffffffffu, good)) return false;
     q[qi(2 * RZ)] = lds4(Ubase + un * (L::Q_STRIDE / 4) + qofs);
     if constexpr (L::LEAD) {
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
     const float4 c = q[qi(RZ)];
     if constexpr (L::LEAD) {
       // the centre halo box arrives with the per-point tiles
-      good = mbar_wait_bounded(&fullP[ps], phase_ps, abort_flag, kWaitLimitNs);
+      good = mbar_wait_bounded(&fullP[ps], phase_ps, abort_flag, p.wait_ns);
       if (!__all_sync(0xffffffffu, good)) return false;
     }
     const float* Uc = L::LEAD ? reinterpret_cast<const float*>(Pbase + ps * L::P_BYTES + L::HALO_OFF) + lofs
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
       }
     }
     if constexpr (!L::LEAD) {
-      good = mbar_wait_bounded(&fullP[ps], phase_ps, abort_flag, kWaitLimitNs);
+      good = mbar_wait_bounded(&fullP[ps], phase_ps, abort_flag, p.wait_ns);
       if (!__all_sync(0xffffffffu, good)) return false;
     }
     const unsigned char* Pst = Pbase + ps * L::P_BYTES;

@@ -73,6 +73,7 @@ struct wave_context {
   int64_t timed[WAVE_KERNEL_KINDS] = {};  // launches whose duration was taken with events
   double ms[WAVE_KERNEL_KINDS] = {};      // summed duration of the timed launches
   int ckpt_interval = 0;
+  unsigned long long wait_ns = kWaitLimitNs;  // limit of the step kernels' progress waits
   int last_plan[4] = {0, 0, 0, 0};  // fmt, buffer levels, parts per segment, segments
   // side stream and events that copy finished receiver rows to a pinned host
   // buffer while later time steps run (created on first use)
@@ -461,6 +462,7 @@ int prepare(wave_context* ctx, const wave_geometry* geom, float dt, int nt, int 
   sp.slabs_x = P->slabs_x;
   sp.slabs_y = P->slabs_y;
   sp.status = ctx ? ctx->d_status : nullptr;  // no context: host-only queries
+  sp.wait_ns = ctx ? ctx->wait_ns : kWaitLimitNs;
   // grid: x tiles, axis-1 tiles, chunks of the streamed axis
   const int tx = (g.NX + step_bx() - 1) / step_bx();
   const int ty = (g.NY + step_by(P->R, nd, sp.iso != 0) - 1) / step_by(P->R, nd, sp.iso != 0);
@@ -1625,6 +1627,12 @@ int wave_context_trim(wave_context* ctx) {
 int wave_context_set_checkpoint_interval(wave_context* ctx, int steps) {
   if (!ctx || steps < 0) return WAVE_ERR_INVALID_ARG;
   ctx->ckpt_interval = steps;
+  return WAVE_OK;
+}
+
+int wave_context_set_wait_limit_ns(wave_context* ctx, uint64_t ns) {
+  if (!ctx) return WAVE_ERR_INVALID_ARG;
+  ctx->wait_ns = ns == 0 ? kWaitLimitNs : static_cast<unsigned long long>(ns);
   return WAVE_OK;
 }
 

@@ -15,7 +15,9 @@ constexpr int kDevOk = 0;
 constexpr int kDevTimeout = 1;
 
 // Bounded waits: a kernel gives up after this many nanoseconds of waiting on
-// one barrier phase, records kDevTimeout and returns.
+// one barrier phase, records kDevTimeout and returns.  This is the default of
+// the progress waits (StepParams::wait_ns, settable per context) and the fixed
+// limit of the drain waits that let a CTA's issued copies land before it exits.
 constexpr unsigned long long kWaitLimitNs = 10ull * 1000ull * 1000ull * 1000ull;
 
 // ---------------------------------------------------------------------------
@@ -211,6 +213,7 @@ struct StepParams {
   const float* scale_in;   // slab scales of that level
   int slabs_x, slabs_y;    // slab grid per plane
   int* status;             // device status word
+  unsigned long long wait_ns;  // limit of each progress wait (the drain waits keep kWaitLimitNs)
 };
 
 // Host-side launcher for one (R, NDIM, MODE); defined in step_r<R>.cu.

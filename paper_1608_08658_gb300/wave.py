@@ -66,6 +66,7 @@ _SIGS = {
     "wave_context_workspace_bytes": (ctypes.c_size_t, [_P]),
     "wave_context_trim": (ctypes.c_int, [_P]),
     "wave_context_set_checkpoint_interval": (ctypes.c_int, [_P, ctypes.c_int]),
+    "wave_context_set_wait_limit_ns": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "wave_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "wave_last_error": (ctypes.c_char_p, [_P]),
     "wave_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, ctypes.c_int, _P]),
@@ -276,6 +277,10 @@ class Context:
 
     def set_checkpoint_interval(self, steps):
         _check(self, lib().wave_context_set_checkpoint_interval(self.handle, int(steps)))
+
+    def set_wait_limit_ns(self, ns):
+        """Limit of each bounded wait of the step kernels (0 = the default 10 s)."""
+        _check(self, lib().wave_context_set_wait_limit_ns(self.handle, int(ns)))
 
     def set_profiling(self, enable):
         _check(self, lib().wave_context_set_profiling(self.handle, int(bool(enable))))

@@ -136,3 +136,28 @@ def test_grid_beyond_one_launch_is_rejected(ctx):
     d = wave.wave_forward(ctx, g2, m2, src, q, rec, dt2, 5, 4)
     ref = oracle.wave.forward(og, m2, dt2, 5, 4, q, src, rec).d
     assert rel_l2(d, ref) <= 1e-4
+
+
+def test_bounded_wait_runs_out_and_context_recovers():
+    """Failure detection without a fault: with the progress-wait limit at 1 ns
+    the step kernels' waits for their tile loads run out; each CTA records the
+    timeout, lets its own copies land and returns, and the call reports
+    WAVE_ERR_TIMEOUT.  The same context, with the default limit restored, then
+    runs a normal forward that matches the oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    so, nt = 8, 12
+    og, m, dt, src, rec, r = _case((83, 37, 40), (10.0, 10.0, 10.0), 4, so, nrec=11)
+    _, geom = geometries(og)
+    q = (r.standard_normal((nt, 1)) * 1e2).astype(np.float32)
+    with wave.Context(0) as c:
+        md, qd = _dev(m), _dev(q)
+        c.set_wait_limit_ns(1)
+        with pytest.raises(wave.WaveError) as e:
+            wave.wave_forward(c, geom, md, src, qd, rec, dt, nt, so)
+        assert e.value.code == wave.WAVE_ERR_TIMEOUT
+        assert "bounded wait" in str(e.value)
+        c.set_wait_limit_ns(0)
+        d = wave.wave_forward(c, geom, md, src, qd, rec, dt, nt, so).cpu().numpy()
+    ref = oracle.wave.forward(og, m, dt, nt, so, q, src, rec).d
+    assert rel_l2(d, ref) <= 1e-4
