@@ -349,11 +349,12 @@ WAVE_API int wave_ricker(float* q_out, int nt, float dt, float f0, float t0);
 
 /* ---- allocation-free entry point ------------------------------------------ */
 
-/* The paper has no counterpart to this entry point; it exists for callers that
- * cannot allocate device memory at the time they need the objective: code that
- * runs while a stream is being captured into a CUDA graph, plug-ins whose host
- * application owns every device allocation through its own pool, or services
- * that must not touch the allocator once a run has started.
+/* The paper has no counterpart to this entry point.  It exists for callers
+ * that cannot allocate device memory at the time they need the objective:
+ * plug-ins whose host application owns every device allocation through its own
+ * pool, and services that must not touch the allocator once a run has started
+ * (an allocation there can stall on a device-wide synchronisation or fail under
+ * memory pressure at the worst moment).
  *
  * wave_objective_noalloc computes the residual r = d - d_obs and the objective
  * phi = 0.5 * sum r^2 (FP64 accumulation) of Eq. 2 for n receiver samples, the
@@ -365,10 +366,13 @@ WAVE_API int wave_ricker(float* q_out, int nt, float dt, float f0, float t0);
  *   d, d_obs: device arrays of n float32 on the current CUDA device;
  *   r_out:    device array of n float32 receiving r, or NULL;
  *   phi_out:  host double receiving phi;
- *   stream:   CUDA stream (NULL = legacy default); the call returns after the
- *             stream has completed its work.
+ *   stream:   CUDA stream (NULL = legacy default); the call copies phi to the
+ *             host and returns after the stream has completed its work.
  * The first call on a device looks up the scratch array's device address (with
- * that device current); make that first call before any stream capture.
+ * that device current); make that first call before any stream capture.  The
+ * address is kept per device together with the id of the CUDA context it was
+ * found in: after a device reset (cudaDeviceReset) the next call sees a new
+ * context and looks the address up again.
  * Every call on a device shares the same scratch and overwrites it; calls that
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.  Nothing in the scratch needs to start at zero.

@@ -1,13 +1,15 @@
 // Allocation-free objective entry point (wave_objective_noalloc).
 //
-// Some callers cannot allocate device memory: code running while a stream is
-// being captured into a CUDA graph, plug-ins embedded in a host application
-// that owns all device allocations through its own pool, or processes that
-// must not touch the allocator once a run has started.  For them this file
-// provides one entry point that needs no workspace from the caller and calls
-// no allocating routine: its per-block partial sums live in a file-scope
-// device array of fixed size that every GPU loading the library keeps until
-// the process exits.
+// Some callers cannot allocate device memory when they need the objective:
+// plug-ins embedded in a host application that owns every device allocation
+// through its own pool, or services that must not touch the allocator once a
+// run has started (an allocation there can stall on a device-wide
+// synchronisation or fail under memory pressure at the worst moment).  For
+// them this file provides one entry point that needs no workspace from the
+// caller and calls no allocating routine: its per-block partial sums live in a
+// file-scope device array of fixed size that every GPU loading the library
+// keeps until the process exits.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -62,22 +64,61 @@ __global__ void chunk_total_kernel(double* partials, int nb) {
   if (threadIdx.x == 0) partials[kMaxBlocks] = 0.5 * sh[0];
 }
 
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
 std::mutex g_mu;
-double* g_scratch_addr[kMaxDevices] = {};
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+// Per device: the scratch array's device address and the id of the context it
+// was looked up in.  A device reset destroys that context and may reload the
+// module elsewhere; the next context gets a new id, so a stale address is
+// never used.
+struct ScratchAddr {
+  unsigned long long ctx_id = 0;
+  double* addr = nullptr;
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
+
+// Unique id of the context current on this thread; WAVE_ERR_CUDA when there is
+// none or the driver cannot report it.
+int current_context_id(unsigned long long* id) {
+  if (!g_ctx_current || !g_ctx_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) {
+      cudaGetLastError();
+      return WAVE_ERR_CUDA;
+    }
+    g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+    g_ctx_id = reinterpret_cast<CtxGetIdFn>(f2);
+  }
+  CUcontext c = nullptr;
+  if (g_ctx_current(&c) != CUDA_SUCCESS || !c || g_ctx_id(c, id) != CUDA_SUCCESS) return WAVE_ERR_CUDA;
+  return WAVE_OK;
+}
 
 // Device address of the scratch array on `dev` (the current device).  The
-// host-side symbol is only a stand-in; the address must come from the runtime.
+// host-side symbol is only a stand-in; the address must come from the runtime,
+// once per device and context.
 int scratch_for(int dev, double** out) {
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
+  unsigned long long id = 0;
+  if (current_context_id(&id) != WAVE_OK) return WAVE_ERR_CUDA;
+  ScratchAddr& e = g_scratch_addr[dev];
+  if (!e.addr || e.ctx_id != id) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_objective_scratch) != cudaSuccess || !p) {
       cudaGetLastError();
       return WAVE_ERR_CUDA;
     }
-    g_scratch_addr[dev] = static_cast<double*>(p);
+    e.addr = static_cast<double*>(p);
+    e.ctx_id = id;
   }
-  *out = g_scratch_addr[dev];
+  *out = e.addr;
   return WAVE_OK;
 }
 

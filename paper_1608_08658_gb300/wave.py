@@ -576,14 +576,41 @@ def wave_ricker(nt, dt, f0, t0=None, out=None):
     return out
 
 
+def _noalloc_array(name, x, n=None):
+    """Checks one array argument of wave_objective_noalloc without touching
+    the GPU: a contiguous float32 torch tensor (of n elements when n is given)."""
+    if not _is_torch(x):
+        raise TypeError("%s must be a torch tensor on a CUDA device" % name)
+    import torch
+    if x.dtype != torch.float32:
+        raise TypeError("%s must be float32, got %s" % (name, x.dtype))
+    if not x.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if n is not None and x.numel() != n:
+        raise ValueError("%s has %d elements, expected %d" % (name, x.numel(), n))
+
+
 def wave_objective_noalloc(d, d_obs, r_out=None, stream=None):
-    """(phi, r) of Eq. 2 for device tensors d, d_obs without any allocation in
-    the library (r is written into ``r_out`` when given)."""
-    d = _f32(d)
-    d_obs = _f32(d_obs)
-    n = int(d.numel()) if _is_torch(d) else int(d.size)
+    """(phi, r_out) of Eq. 2 for CUDA tensors d, d_obs without any allocation in
+    the library; r = d - d_obs is written into ``r_out`` when given.  Every array
+    is checked (type, size, device) before the call, so a mismatch raises
+    instead of reaching the GPU."""
+    _noalloc_array("d", d)
+    n = int(d.numel())
+    _noalloc_array("d_obs", d_obs, n)
+    if r_out is not None:
+        _noalloc_array("r_out", r_out, n)
+    arrays = [d, d_obs] + ([r_out] if r_out is not None else [])
+    if not all(a.is_cuda for a in arrays):
+        raise ValueError("d, d_obs and r_out must be CUDA tensors")
+    if len({a.device for a in arrays}) != 1:
+        raise ValueError("d, d_obs and r_out must be on the same device")
+    import torch
+    if torch.cuda.current_device() != d.device.index:
+        raise ValueError("the current CUDA device (%d) is not the tensors' device (%s)"
+                         % (torch.cuda.current_device(), d.device))
     phi = ctypes.c_double()
-    st = stream if stream is not None else _stream_for(d, d_obs)
+    st = stream if stream is not None else _stream_for(d)
     rc = lib().wave_objective_noalloc(_ptr(d), _ptr(d_obs), _ptr(r_out), n, ctypes.byref(phi), st)
     if rc != WAVE_OK:
         raise WaveError(rc, "wave_objective_noalloc failed")

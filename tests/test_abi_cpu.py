@@ -111,3 +111,26 @@ def test_step_kernel_layout(lib):
         wave.wave_step_kernel_layout(8, 3, 9, 1)
     with pytest.raises(wave.WaveError):
         wave.wave_step_kernel_layout(8, 4, 0, 1)
+
+
+def test_objective_noalloc_wrapper_rejects_bad_arrays_before_any_call(monkeypatch):
+    """The Python wrapper of wave_objective_noalloc checks every array (type,
+    dtype, contiguity, size, device) before it reaches the library: none of
+    these calls launches anything."""
+    torch = pytest.importorskip("torch")
+
+    def no_call():
+        raise AssertionError("the library must not be called")
+    monkeypatch.setattr(wave, "lib", no_call)
+    d = torch.zeros(10)
+    bad = [((np.zeros(10, np.float32), d), {}, TypeError),                       # not a tensor
+           ((d, torch.zeros(9)), {}, ValueError),                                 # d_obs too short
+           ((d, torch.zeros(10, dtype=torch.float64)), {}, TypeError),            # d_obs not float32
+           ((d, d), {"r_out": torch.zeros(9)}, ValueError),                       # r_out too short
+           ((d, d), {"r_out": torch.zeros(10, dtype=torch.float64)}, TypeError),  # r_out not float32
+           ((d, d), {"r_out": torch.zeros(20)[::2]}, ValueError),                # r_out not contiguous
+           ((torch.zeros(20)[::2], torch.zeros(10)), {}, ValueError),             # d not contiguous
+           ((d, d), {}, ValueError)]                                              # host tensors
+    for args, kw, exc in bad:
+        with pytest.raises(exc):
+            wave.wave_objective_noalloc(*args, **kw)
