@@ -10,6 +10,7 @@ restatement of the method in float64, written from the paper:
   * ``fd``      -- central second-derivative weights of even order (Sec. IV-A1),
   * ``model``   -- padding, sponge profile, CFL limit, Ricker wavelet (Sec. V-C/D),
   * ``interp``  -- sparse-point (bi/tri-linear) interpolation operators (Sec. IV),
+  * ``snapshot`` -- the 16-bit storage of the forward wavefield that Eq. 3 reads,
   * ``wave``    -- Laplacian, forward leapfrog (Listing 1, Eq. 1), adjoint
                    (Listing 2, Eq. 4), objective (Eq. 2), gradient (Eq. 3),
                    and the linearised (Born) operator J whose transpose Eq. 3
@@ -22,4 +23,4 @@ itself (closed forms, brute-force dense solves, moment conditions, adjoint and
 Taylor identities).
 """
 
-from . import fd, model, interp, wave  # noqa: F401
+from . import fd, model, interp, snapshot, wave  # noqa: F401

@@ -40,6 +40,7 @@ import scipy.sparse as sp
 from .fd import fd_weights, radius
 from .interp import interpolation_matrix
 from .model import damping, fold_gradient, pad_model
+from .snapshot import round_level
 
 
 def _odd_pad(u, R):
@@ -187,16 +188,25 @@ def objective(geom, m_phys, dt, nt, space_order, q, src_coords, rec_coords, d_ob
     return 0.5 * float(np.sum(r * r))
 
 
-def gradient(geom, m_phys, dt, nt, space_order, q, src_coords, rec_coords, d_obs):
-    """Eq. 3 gradient of Eq. 2 on the physical grid, and the objective value."""
+def gradient(geom, m_phys, dt, nt, space_order, q, src_coords, rec_coords, d_obs, snapshot_rounding=None):
+    """Eq. 3 gradient of Eq. 2 on the physical grid, and the objective value.
+
+    ``snapshot_rounding`` ("bf16" or "fp16") evaluates the imaging condition on
+    the stored forward levels u^1..u^{nt-1} as the 16-bit storage reads them
+    back (``snapshot.round_level``); the forward and adjoint sweeps themselves
+    are unchanged.
+    """
     m = pad_model(geom, m_phys)
     eta = damping(geom)
     Ps, Pr = operators(geom, src_coords, rec_coords)
     fwd = forward_op(m, eta, geom.spacing, dt, nt, space_order, q, Ps, Pr, save=True)
     resid = fwd.d - np.asarray(d_obs, dtype=np.float64)
     phi = 0.5 * float(np.sum(resid * resid))
+    history = fwd.history
+    if snapshot_rounding is not None:
+        history = [history[0]] + [round_level(u, snapshot_rounding) for u in history[1:]]
     _, g = adjoint_op(m, eta, geom.spacing, dt, nt, space_order, resid, Ps, Pr,
-                      u_history=fwd.history)
+                      u_history=history)
     return fold_gradient(geom, g), phi
 
 

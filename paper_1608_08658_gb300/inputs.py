@@ -231,3 +231,18 @@ def layered_salt_velocity(shape_xyz, spacing, n_layers=8, v_min=1.5, v_max=4.5, 
         zz = ((k * spacing[2] - c[2]) / semi_axes_m[2]) ** 2
         v[k] = np.where(xy + zz <= 1.0, np.float32(v_salt), prof[k])
     return v
+
+
+def layered_starting_velocity(shape_xyz, spacing, n_layers=8, v_min=1.5, v_max=4.5, sigma_m=150.0, seed=5):
+    """Starting model of the large-model gradient: the flat layers of
+    ``layered_salt_velocity`` (same seed) smoothed along depth by a Gaussian of
+    standard deviation sigma_m (edge values repeated), without the salt body;
+    float32, [nz][ny][nx]."""
+    nx, ny, nz = shape_xyz
+    prof = layered_profile(nz, spacing[2], n_layers, v_min, v_max, seed=seed)
+    k = int(np.ceil(4.0 * sigma_m / spacing[2]))
+    t = np.arange(-k, k + 1) * spacing[2] / sigma_m
+    w = np.exp(-0.5 * t * t)
+    w /= w.sum()
+    smooth = np.convolve(np.pad(prof, k, mode="edge"), w, mode="valid").astype(np.float32)
+    return np.broadcast_to(smooth[:, None, None], (nz, ny, nx)).copy()

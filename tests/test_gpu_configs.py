@@ -73,8 +73,9 @@ def test_fwi_gradient_storage_modes_full_size(ctx):
     e16 = _rel(g["full_fp16"][0], g["auto"][0])
     ebf = _rel(g["full_bf16"][0], g["auto"][0])
     print("336^3 nt1500 gradient: FP16 snapshots rel-L2 %.2e, BF16 %.2e vs FP32" % (e16, ebf))
+    # measured on this workload: 2.4e-4 (FP16) and 1.9e-3 (BF16); gates at about twice that
     assert e16 <= 5e-4
-    assert ebf <= 5e-3
+    assert ebf <= 4e-3
     # the autograd.Function backward is the same adjoint-state computation
     op = WaveOperator(ctx, geom, src, rec, dt, nt, so, snap_mode="auto")
     mt_ = m0d.clone().requires_grad_(True)
@@ -162,4 +163,36 @@ def test_large_model_sampled_two_steps(ctx):
             worst = max(worst, err)
             assert err <= 1e-5, ((z, y, x), got, want)
     print("large-model sampled two-step parity: worst error %.2e of local scale" % worst)
+    ctx.trim()
+
+
+def test_large_salt_gradient_bf16_against_fp32(ctx):
+    """Large workload at its full grid (1080 x 1080 x 680 points, order 16) and a
+    shorter time axis: observed data from the layered model with the salt body,
+    the gradient at the depth-smoothed layers without the salt.  The objective
+    is not zero (the smoothed near-surface layers change the early arrivals),
+    and the gradient with BF16 checkpointed snapshots is compared with the FP32
+    checkpointed one; the objective of both is the same forward sweep."""
+    so, nt = 16, 1200
+    shape, h = (1000, 1000, 600), (10.0, 10.0, 10.0)
+    geom = wave.Geometry(shape=shape, spacing=h, nbl=40, sponge_vref=4.5)
+    dt = f32(0.4 * wave.wave_dt_max(h, so, 4.5))
+    src = np.array([[4995.0, 4995.0, 20.0]], dtype=np.float32)
+    gx = np.linspace(0.0, 9990.0, 100)
+    X, Y = np.meshgrid(gx, gx, indexing="xy")
+    rec = np.stack([X.ravel(), Y.ravel(), np.full(X.size, 20.0)], axis=1).astype(np.float32)
+    qd = torch.from_numpy(wave.wave_ricker(nt, dt, 0.010).reshape(nt, 1)).cuda()
+    mt = torch.from_numpy(inputs.slowness2(inputs.layered_salt_velocity(shape, h))).cuda()
+    d_obs = wave.wave_forward(ctx, geom, mt, src, qd, rec, dt, nt, so)
+    del mt
+    m0 = torch.from_numpy(inputs.slowness2(inputs.layered_starting_velocity(shape, h))).cuda()
+    g32, phi32 = wave.wave_gradient(ctx, geom, m0, src, qd, rec, d_obs, dt, nt, so, snap_mode="checkpoint_fp32")
+    g32 = g32.clone()
+    gbf, phibf = wave.wave_gradient(ctx, geom, m0, src, qd, rec, d_obs, dt, nt, so, snap_mode="checkpoint_bf16")
+    e = _rel(gbf, g32)
+    print("large salt model, so16 nt%d: objective %.6e, |g| %.3e, BF16-checkpointed vs FP32 gradient rel-L2 %.2e"
+          % (nt, phi32, float(g32.double().norm()), e))
+    assert phi32 > 0.0 and float(g32.abs().max()) > 0.0
+    assert phibf == phi32
+    assert e <= 4e-3
     ctx.trim()

@@ -88,3 +88,21 @@ def test_generators_are_deterministic(seed):
     b = inputs.random_points(10, (30, 20, 10), (10.0, 10.0, 10.0), seed)
     np.testing.assert_array_equal(a, b)
     np.testing.assert_array_equal(inputs.random_traces(5, 3, seed), inputs.random_traces(5, 3, seed))
+
+
+def test_large_starting_model_is_the_smoothed_layers_without_salt():
+    shape, h = (40, 30, 600), (10.0, 10.0, 10.0)
+    vt = inputs.layered_salt_velocity(shape, h)
+    v0 = inputs.layered_starting_velocity(shape, h)
+    prof = inputs.layered_profile(600, 10.0, 8, 1.5, 4.5, seed=5)
+    assert v0.shape == vt.shape and v0.dtype == np.float32
+    assert np.all(v0 == v0[:, :1, :1])                    # flat layers only: no salt body
+    assert np.any(vt == 4.5) and not np.any(v0 > prof.max() + 1e-6)
+    # far (> 4 sigma) from every interface the smoothing leaves the layer value
+    cuts = np.nonzero(np.diff(prof))[0] + 1
+    far = np.array([np.all(np.abs(k - cuts) > 61) for k in range(600)])
+    np.testing.assert_allclose(v0[far, 0, 0], prof[far], rtol=1e-6)
+    # at an interface the starting model lies strictly between the two layers, and it is monotone
+    for k in cuts:
+        lo, hi = sorted((prof[k - 1], prof[k]))
+        assert lo < v0[k, 0, 0] < hi
