@@ -146,15 +146,25 @@ WAVE_API int wave_context_set_checkpoint_interval(wave_context* ctx, int steps);
 
 /* Limit, in nanoseconds, of each bounded wait by which a stencil-step kernel
  * waits for its tile loads or for its own consumer warps (failure detection;
- * the paper has no counterpart).  A kernel whose wait runs out records a
+ * the paper has no counterpart).  A wait first suspends in hardware for a
+ * short system-dependent window, in which waits for data normally complete;
+ * the limit counts from there.  A kernel whose wait runs out records a
  * timeout in the context's device status word, lets every copy it has issued
  * land (those drain waits keep the default limit, so no CTA exits with a copy
  * in flight) and returns; the call then returns WAVE_ERR_TIMEOUT and the
- * context stays usable.  ns = 0 restores the default of 10 s.  A very small
- * limit makes ordinary waits for data run out; it exists so that tests can
- * exercise the timeout path without a fault or a hang.  Sessions take the
- * limit in force when they are created.  Errors: INVALID_ARG (ctx NULL). */
+ * context stays usable.  ns = 0 restores the default of 10 s.  Sessions take
+ * the limit in force when they are created.  Errors: INVALID_ARG (ctx NULL). */
 WAVE_API int wave_context_set_wait_limit_ns(wave_context* ctx, uint64_t ns);
+
+/* Test hook of the same failure-detection path (no counterpart in the paper):
+ * the context's next stencil-step launch issues none of its tile loads, so
+ * every wait of its consumer warps runs out after the wait limit, the kernel
+ * records the timeout and returns, and the call returns WAVE_ERR_TIMEOUT.
+ * Nothing faults and no wait is unbounded; later launches run normally.  Set a
+ * short limit first: with the default, each wave of resident CTAs of that one
+ * launch waits 10 s.  A session captured after this call takes the withheld
+ * launch into its graph.  Errors: INVALID_ARG (ctx NULL). */
+WAVE_API int wave_context_withhold_next_loads(wave_context* ctx);
 
 /* Storage plan of the context's last wave_gradient / wave_jacobian_adjoint
  * call: snapshot buffer levels F, parts per checkpointed segment k, and the

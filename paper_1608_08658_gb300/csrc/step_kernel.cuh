@@ -146,6 +146,9 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
 
   // ------------------------------------------------------------------ producer
   if (warp == T::NCW) {
+    // failure-detection test hook: with no load issued, the consumers' waits
+    // run out after p.wait_ns and take the timeout path; nothing is in flight
+    if (p.withhold) return;
     if (lane == 0) {
       prefetch_tensormap(&tm_u);
       prefetch_tensormap(&tm_p);

@@ -74,6 +74,7 @@ struct wave_context {
   double ms[WAVE_KERNEL_KINDS] = {};      // summed duration of the timed launches
   int ckpt_interval = 0;
   unsigned long long wait_ns = kWaitLimitNs;  // limit of the step kernels' progress waits
+  bool withhold_next = false;                 // test hook: the next step launch issues no loads
   int last_plan[4] = {0, 0, 0, 0};  // fmt, buffer levels, parts per segment, segments
   // side stream and events that copy finished receiver rows to a pinned host
   // buffer while later time steps run (created on first use)
@@ -810,7 +811,12 @@ int step(wave_context* ctx, Prob& P, Work& W, int mode, int cur, int prev, cudaS
   P.sp.prev = prev;
   const int kind = mode_is_grad(mode) ? WAVE_KERNEL_STEP_GRAD
                                       : (mode_is_snap(mode) ? WAVE_KERNEL_STEP_SNAP : WAVE_KERNEL_STEP);
-  return launch(ctx, kind, s, [&] { return launch_step(P.R, P.ndim, mode, W.maps, P.sp, P.grid, s); });
+  StepParams sp = P.sp;
+  if (ctx->withhold_next) {
+    sp.withhold = 1;
+    ctx->withhold_next = false;
+  }
+  return launch(ctx, kind, s, [&] { return launch_step(P.R, P.ndim, mode, W.maps, sp, P.grid, s); });
 }
 
 struct SnapStore {
@@ -1633,6 +1639,12 @@ int wave_context_set_checkpoint_interval(wave_context* ctx, int steps) {
 int wave_context_set_wait_limit_ns(wave_context* ctx, uint64_t ns) {
   if (!ctx) return WAVE_ERR_INVALID_ARG;
   ctx->wait_ns = ns == 0 ? kWaitLimitNs : static_cast<unsigned long long>(ns);
+  return WAVE_OK;
+}
+
+int wave_context_withhold_next_loads(wave_context* ctx) {
+  if (!ctx) return WAVE_ERR_INVALID_ARG;
+  ctx->withhold_next = true;
   return WAVE_OK;
 }
 

@@ -214,6 +214,7 @@ struct StepParams {
   int slabs_x, slabs_y;    // slab grid per plane
   int* status;             // device status word
   unsigned long long wait_ns;  // limit of each progress wait (the drain waits keep kWaitLimitNs)
+  int withhold;            // test hook: 1 = the producer issues no tile loads (every consumer wait runs out)
 };
 
 // Host-side launcher for one (R, NDIM, MODE); defined in step_r<R>.cu.

@@ -139,11 +139,12 @@ def test_grid_beyond_one_launch_is_rejected(ctx):
 
 
 def test_bounded_wait_runs_out_and_context_recovers():
-    """Failure detection without a fault: with the progress-wait limit at 1 ns
-    the step kernels' waits for their tile loads run out; each CTA records the
-    timeout, lets its own copies land and returns, and the call reports
-    WAVE_ERR_TIMEOUT.  The same context, with the default limit restored, then
-    runs a normal forward that matches the oracle."""
+    """Failure detection without a fault: one step launch issues none of its
+    tile loads (a barrier phase that nothing completes), so with the wait
+    limit at 2 ms its consumers' waits run out; each CTA records the timeout
+    and returns, and the call reports WAVE_ERR_TIMEOUT.  The same context, with
+    the default limit restored, then runs a normal forward that matches the
+    oracle."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     so, nt = 8, 12
@@ -152,11 +153,13 @@ def test_bounded_wait_runs_out_and_context_recovers():
     q = (r.standard_normal((nt, 1)) * 1e2).astype(np.float32)
     with wave.Context(0) as c:
         md, qd = _dev(m), _dev(q)
-        c.set_wait_limit_ns(1)
+        c.set_wait_limit_ns(2_000_000)
+        c.withhold_next_loads()
         with pytest.raises(wave.WaveError) as e:
             wave.wave_forward(c, geom, md, src, qd, rec, dt, nt, so)
         assert e.value.code == wave.WAVE_ERR_TIMEOUT
         assert "bounded wait" in str(e.value)
+        # only the one launch withholds its loads: the next call succeeds
         c.set_wait_limit_ns(0)
         d = wave.wave_forward(c, geom, md, src, qd, rec, dt, nt, so).cpu().numpy()
     ref = oracle.wave.forward(og, m, dt, nt, so, q, src, rec).d
