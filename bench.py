@@ -51,9 +51,15 @@ def parse_args():
     ap.add_argument("--so", type=int, default=8)
     ap.add_argument("--nbl", type=int, default=40)
     ap.add_argument("--snap", default="checkpoint_fp32")
-    ap.add_argument("--mode", default="gradient", choices=["gradient", "forward", "serve"],
+    ap.add_argument("--mode", default="gradient", choices=["gradient", "forward", "serve", "sweep"],
                     help="gradient: one FWI gradient per step (default); forward: one forward modelling per step; "
-                         "serve: a Poisson stream of shot-modelling requests through the continuous-batching server")
+                         "serve: a Poisson stream of shot-modelling requests through the continuous-batching server; "
+                         "sweep: forward modelling per space order (--orders) on the throughput workload, with the "
+                         "per-launch times of every step-kernel kind")
+    ap.add_argument("--orders", default="2,4,6,8,10,12,14,16", help="sweep mode: space orders")
+    ap.add_argument("--kernel-nt", type=int, default=160,
+                    help="sweep mode: time levels of the full-storage gradients that time the snapshot and "
+                         "imaging steps (0 = forward only)")
     ap.add_argument("--requests", type=int, default=400, help="serve mode: number of requests")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serve mode: HBM budget for resident requests")
     ap.add_argument("--max-resident", type=int, default=32, help="serve mode: stream slots")
@@ -531,6 +537,95 @@ def run_serve(args, rank, world, local_rank):
     return 0
 
 
+def run_sweep(args, rank, world, local_rank):
+    """Forward modelling of the throughput workload (n^3 two-layer model with
+    the 5 % perturbation, 40-point layer, equal spacing) for each space order:
+    W untimed and K timed runs of nt steps (Gpts/s = points (nt-1) / time), and
+    per-launch CUDA-event times of the plain step; with --kernel-nt > 0, also of
+    the snapshot and imaging steps of full-storage gradients (FP32 and FP16
+    snapshots) at that many time levels.  One JSON line; a table on stderr."""
+    import torch
+    from paper_1608_08658_gb300 import wave
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    orders = [int(x) for x in args.orders.split(",")]
+    w = make_workload(args.n, args.nbl, 8, args.nt)
+    geom = wave.Geometry(shape=w["shape"], spacing=w["spacing"], nbl=w["nbl"], sponge_vref=w["vmax"])
+    npts = int(np.prod([s + 2 * w["nbl"] for s in w["shape"]]))
+    m = torch.from_numpy((1.0 / w["v_true"] ** 2).astype(np.float32)).to(dev)
+    src = torch.from_numpy(w["src"]).to(dev)
+    rec = torch.from_numpy(w["rec"]).to(dev)
+    peak, peak_kind = hbm_peak()
+    bpp = {"plain": 16, "snap_fp32": 20, "grad_fp32": 28, "snap_fp16": 18, "grad_fp16": 26}
+    rows = []
+    launches = 0
+    clocks = ClockSampler() if rank == 0 else None
+    with wave.Context(local_rank) as ctx:
+        for so in orders:
+            dt = 0.4 * wave.wave_dt_max(w["spacing"], so, w["vmax"])
+            q = torch.from_numpy(wave.wave_ricker(args.nt, dt, w["f0"]).reshape(args.nt, 1)).to(dev)
+            d = wave.wave_forward(ctx, geom, m, src, q, rec, dt, args.nt, so)
+            for _ in range(args.warmup):
+                wave.wave_forward(ctx, geom, m, src, q, rec, dt, args.nt, so, d_out=d)
+            torch.cuda.synchronize()
+            ctx.reset_stats()
+            ctx.set_profiling(True)
+            stream = torch.cuda.current_stream(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                wave.wave_forward(ctx, geom, m, src, q, rec, dt, args.nt, so, d_out=d)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ctx.set_profiling(False)
+            ms = e0.elapsed_time(e1) / args.steps
+            launches += ctx.kernel_stats(-1)[0]
+            cnt, tms = ctx.kernel_stats(0)
+            row = {"space_order": so, "forward_ms": ms, "forward_gpts": npts * (args.nt - 1) / (ms * 1e-3) / 1e9,
+                   "kernels_ms": {"plain": tms / cnt}}
+            if args.kernel_nt > 0:
+                kn = args.kernel_nt
+                qk = q[:kn].contiguous()
+                dk = wave.wave_forward(ctx, geom, m, src, qk, rec, dt, kn, so)
+                for fmt in ("fp32", "fp16"):
+                    wave.wave_gradient(ctx, geom, m * 1.01, src, qk, rec, dk, dt, kn, so, snap_mode="full_" + fmt)
+                    torch.cuda.synchronize()
+                    ctx.reset_stats()
+                    ctx.set_profiling(True)
+                    for _ in range(2):
+                        wave.wave_gradient(ctx, geom, m * 1.01, src, qk, rec, dk, dt, kn, so,
+                                           snap_mode="full_" + fmt)
+                    torch.cuda.synchronize()
+                    ctx.set_profiling(False)
+                    launches += ctx.kernel_stats(-1)[0]
+                    for k, name in ((1, "snap_" + fmt), (2, "grad_" + fmt)):
+                        cnt, tms = ctx.kernel_stats(k)
+                        if cnt:
+                            row["kernels_ms"][name] = tms / cnt
+                ctx.trim()
+            row["hbm_frac"] = {k: bpp[k] * npts / (v * 1e-3) / 1e9 / peak for k, v in row["kernels_ms"].items()}
+            rows.append(row)
+            print("so %2d  forward %.1f Gpts/s  " % (so, row["forward_gpts"]) + "  ".join(
+                "%s %.4f ms (%.1f %%)" % (k, v, 100 * row["hbm_frac"][k]) for k, v in row["kernels_ms"].items()),
+                file=sys.stderr, flush=True)
+    clk = clocks.stop() if clocks else None
+    if rank == 0:
+        main_row = next((r for r in rows if r["space_order"] == 8), rows[0])
+        comp = w["shape"][0] + 2 * w["nbl"]
+        line = {"metric": METRIC, "value": main_row["forward_gpts"], "unit": "Gpts/s", "n_gpus": 1,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": main_row["forward_ms"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": "3D forward modelling per space order %s: %d^3 + %d sponge = %d^3 points, "
+                                       "h=10 m, two-layer 1.5/2.5 km/s + 5%% perturbation, nt=%d; value at order %d"
+                                       % (args.orders, args.n, w["nbl"], comp, args.nt, main_row["space_order"]),
+                           "kernel_nt": args.kernel_nt, "l2": "inputs larger than L2"},
+                "sweep": rows, "peak_gbs": peak, "peak_source": peak_kind, "bytes_per_point": bpp,
+                "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def ctypes_stream(stream):
     import ctypes
     return ctypes.c_void_p(stream.cuda_stream)
@@ -547,6 +642,8 @@ def main():
         return run_reference(args, rank, world)
     if args.mode == "serve":
         return run_serve(args, rank, world, local_rank)
+    if args.mode == "sweep":
+        return run_sweep(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 

@@ -98,6 +98,80 @@ __device__ __forceinline__ bool call_in_order(F& f, IntC<I>, IntC<N>) {
   }
 }
 
+// Producer warp of a step kernel (layout L: StepLayout or TallLayout).  Lane
+// 0 streams the CTA's planes through the two rings: the queue-feed stage of
+// sequence s (the centre-level halo plane z0 - RZ + s, or in the lead-plane
+// layout its interior box) and, from s = 2 RZ on, the per-point stage of plane
+// j = s - 2 RZ (previous level, cm, and g / snapshot by mode; plus the centre
+// halo box in the lead-plane layout).  A stage is refilled once the consumer
+// warps have released it.  When a wait runs out, or the consumers abort, the
+// producer records the timeout and lets every copy it issued land.
+template <class L, int R, int MODE>
+__device__ __forceinline__ void produce(const CUtensorMap& tm_u, const CUtensorMap& tm_p, const CUtensorMap& tm_cm,
+                                        const CUtensorMap& tm_g, const CUtensorMap& tm_s, const StepParams& p,
+                                        int x0, int y0, int z0, int nU, uint64_t* fullU, uint64_t* emptyU,
+                                        uint64_t* fullP, uint64_t* emptyP, volatile int* abort_flag, float* Ubase,
+                                        unsigned char* Pbase) {
+  constexpr int RZ = L::RZ;
+  const int lane = threadIdx.x & 31;
+  // failure-detection test hook: with no load issued, the consumers' waits
+  // run out after p.wait_ns and take the timeout path; nothing is in flight
+  if (p.withhold) return;
+  if (lane != 0) return;
+  prefetch_tensormap(&tm_u);
+  prefetch_tensormap(&tm_p);
+  prefetch_tensormap(&tm_cm);
+  if (mode_loads_g(MODE)) prefetch_tensormap(&tm_g);
+  if (mode_is_grad(MODE)) prefetch_tensormap(&tm_s);
+  int issuedU = 0, issuedP = 0;
+  bool ok = true;
+  for (int s = 0; s < nU; ++s) {
+    const int slot = s % L::NSU;
+    if (s >= L::NSU) ok = mbar_wait_bounded(&emptyU[slot], ((s / L::NSU) - 1) & 1, abort_flag, p.wait_ns);
+    if (!ok) break;
+    mbar_arrive_expect_tx(&fullU[slot], L::Q_BYTES);
+    if constexpr (L::LEAD)
+      tma_load_4d(Ubase + slot * (L::Q_STRIDE / 4), &tm_p, x0, y0, z0 - RZ + s, p.cur, &fullU[slot]);
+    else
+      tma_load_4d(Ubase + slot * (L::Q_STRIDE / 4), &tm_u, x0 - L::HX, y0 - R, z0 - RZ + s, p.cur, &fullU[slot]);
+    issuedU = s + 1;
+    if (s >= 2 * RZ) {
+      const int j = s - 2 * RZ;
+      const int ps = j % L::NSP;
+      if (j >= L::NSP) ok = mbar_wait_bounded(&emptyP[ps], ((j / L::NSP) - 1) & 1, abort_flag, p.wait_ns);
+      if (!ok) break;
+      unsigned char* pd = Pbase + ps * L::P_BYTES;
+      mbar_arrive_expect_tx(&fullP[ps], L::P_TX);
+      if constexpr (L::LEAD)
+        tma_load_4d(pd + L::HALO_OFF, &tm_u, x0 - L::HX, y0 - R, z0 + j, p.cur, &fullP[ps]);
+      tma_load_4d(pd + L::PREV_OFF, &tm_p, x0, y0, z0 + j, p.prev, &fullP[ps]);
+      tma_load_3d(pd + L::CM_OFF, &tm_cm, x0, y0, z0 + j, &fullP[ps]);
+      if (mode_loads_g(MODE)) tma_load_3d(pd + L::G_OFF, &tm_g, x0, y0, z0 + j, &fullP[ps]);
+      if (mode_is_grad(MODE)) tma_load_4d(pd + L::S_OFF, &tm_s, x0, y0, z0 + j, p.snap_level, &fullP[ps]);
+      issuedP = j + 1;
+    }
+  }
+  if (!ok) {
+    *abort_flag = 1;
+    atomicExch(p.status, kDevTimeout);
+  }
+  if (*abort_flag) {
+    // let every copy this thread issued land before the CTA exits
+    for (int slot = 0; slot < L::NSU; ++slot) {
+      if (issuedU > slot) {
+        const int last = slot + L::NSU * ((issuedU - 1 - slot) / L::NSU);
+        mbar_wait_bounded(&fullU[slot], (last / L::NSU) & 1, nullptr, kWaitLimitNs);
+      }
+    }
+    for (int slot = 0; slot < L::NSP; ++slot) {
+      if (issuedP > slot) {
+        const int last = slot + L::NSP * ((issuedP - 1 - slot) / L::NSP);
+        mbar_wait_bounded(&fullP[slot], (last / L::NSP) & 1, nullptr, kWaitLimitNs);
+      }
+    }
+  }
+}
+
 template <int R, int NDIM, int MODE, bool ISO>
 __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayout<R, NDIM, MODE, ISO>::MIN_BLOCKS))
     step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
@@ -146,63 +220,8 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
 
   // ------------------------------------------------------------------ producer
   if (warp == T::NCW) {
-    // failure-detection test hook: with no load issued, the consumers' waits
-    // run out after p.wait_ns and take the timeout path; nothing is in flight
-    if (p.withhold) return;
-    if (lane == 0) {
-      prefetch_tensormap(&tm_u);
-      prefetch_tensormap(&tm_p);
-      prefetch_tensormap(&tm_cm);
-      if (mode_loads_g(MODE)) prefetch_tensormap(&tm_g);
-      if (mode_is_grad(MODE)) prefetch_tensormap(&tm_s);
-      int issuedU = 0, issuedP = 0;
-      bool ok = true;
-      for (int s = 0; s < nU; ++s) {
-        const int slot = s % L::NSU;
-        if (s >= L::NSU) ok = mbar_wait_bounded(&emptyU[slot], ((s / L::NSU) - 1) & 1, abort_flag, p.wait_ns);
-        if (!ok) break;
-        mbar_arrive_expect_tx(&fullU[slot], L::Q_BYTES);
-        if constexpr (L::LEAD)
-          tma_load_4d(Ubase + slot * (L::Q_STRIDE / 4), &tm_p, x0, y0, z0 - RZ + s, p.cur, &fullU[slot]);
-        else
-          tma_load_4d(Ubase + slot * (L::Q_STRIDE / 4), &tm_u, x0 - T::HX, y0 - R, z0 - RZ + s, p.cur, &fullU[slot]);
-        issuedU = s + 1;
-        if (s >= 2 * RZ) {
-          const int j = s - 2 * RZ;
-          const int ps = j % L::NSP;
-          if (j >= L::NSP) ok = mbar_wait_bounded(&emptyP[ps], ((j / L::NSP) - 1) & 1, abort_flag, p.wait_ns);
-          if (!ok) break;
-          unsigned char* pd = Pbase + ps * L::P_BYTES;
-          mbar_arrive_expect_tx(&fullP[ps], L::P_TX);
-          if constexpr (L::LEAD)
-            tma_load_4d(pd + L::HALO_OFF, &tm_u, x0 - T::HX, y0 - R, z0 + j, p.cur, &fullP[ps]);
-          tma_load_4d(pd + L::PREV_OFF, &tm_p, x0, y0, z0 + j, p.prev, &fullP[ps]);
-          tma_load_3d(pd + L::CM_OFF, &tm_cm, x0, y0, z0 + j, &fullP[ps]);
-          if (mode_loads_g(MODE)) tma_load_3d(pd + L::G_OFF, &tm_g, x0, y0, z0 + j, &fullP[ps]);
-          if (mode_is_grad(MODE)) tma_load_4d(pd + L::S_OFF, &tm_s, x0, y0, z0 + j, p.snap_level, &fullP[ps]);
-          issuedP = j + 1;
-        }
-      }
-      if (!ok) {
-        *abort_flag = 1;
-        atomicExch(p.status, kDevTimeout);
-      }
-      if (*abort_flag) {
-        // let every copy this thread issued land before the CTA exits
-        for (int slot = 0; slot < L::NSU; ++slot) {
-          if (issuedU > slot) {
-            const int last = slot + L::NSU * ((issuedU - 1 - slot) / L::NSU);
-            mbar_wait_bounded(&fullU[slot], (last / L::NSU) & 1, nullptr, kWaitLimitNs);
-          }
-        }
-        for (int slot = 0; slot < L::NSP; ++slot) {
-          if (issuedP > slot) {
-            const int last = slot + L::NSP * ((issuedP - 1 - slot) / L::NSP);
-            mbar_wait_bounded(&fullP[slot], (last / L::NSP) & 1, nullptr, kWaitLimitNs);
-          }
-        }
-      }
-    }
+    produce<L, R, MODE>(tm_u, tm_p, tm_cm, tm_g, tm_s, p, x0, y0, z0, nU, fullU, emptyU, fullP, emptyP,
+                        abort_flag, Ubase, Pbase);
     return;
   }
 

@@ -74,6 +74,7 @@ struct wave_context {
   double ms[WAVE_KERNEL_KINDS] = {};      // summed duration of the timed launches
   int ckpt_interval = 0;
   unsigned long long wait_ns = kWaitLimitNs;  // limit of the step kernels' progress waits
+  int sm_count = 152;                         // multiprocessors of the device
   bool withhold_next = false;                 // test hook: the next step launch issues no loads
   int last_plan[4] = {0, 0, 0, 0};  // fmt, buffer levels, parts per segment, segments
   // side stream and events that copy finished receiver rows to a pinned host
@@ -374,6 +375,34 @@ struct Prob {
   dim3 grid;
 };
 
+// Number of chunks the streamed axis (NZ planes) is cut into; the grid has
+// `tiles` column tiles times that many CTAs, of which `slots` run at once.
+// Rule, from measurements on 592^3 (ms per step launch for 1..9 chunks):
+//   order 8:  0.707 0.610 0.551 0.529 0.557 0.547 0.535 0.530 0.528
+//   order 16: 0.925 0.837 0.829 0.815 0.810 0.797 0.794 0.800 0.802
+// at least 8 waves of CTAs (W = tiles c / slots >= 8), and among the counts
+// from there up to twice that, the fullest last wave (W / ceil(W); the smaller
+// count within 1 %): 9 chunks at order 8, 7 at order 16.  Chunks keep at least
+// max(32, 4R) planes, since each CTA first loads the 2R planes of its z halo;
+// where 8 waves are out of reach, the most chunks allowed are taken.
+int choose_chunks(long long tiles, int NZ, int R, long long slots) {
+  const int cmax = std::max(1, NZ / std::max(32, 4 * R));
+  slots = std::max<long long>(1, slots);
+  if (tiles * cmax < 8 * slots) return cmax;
+  int lo = 1;
+  while (tiles * lo < 8 * slots) ++lo;
+  const int hi = std::min(cmax, 2 * lo);
+  auto fill = [&](int c) {
+    const double w = double(tiles * c) / double(slots);
+    return w / std::ceil(w);
+  };
+  double best_fill = 0.0;
+  for (int c = lo; c <= hi; ++c) best_fill = std::max(best_fill, fill(c));
+  for (int c = lo; c <= hi; ++c)
+    if (fill(c) >= best_fill - 0.01) return c;
+  return lo;
+}
+
 int prepare(wave_context* ctx, const wave_geometry* geom, float dt, int nt, int so, Prob* P) {
   if (!geom) return fail(ctx, WAVE_ERR_INVALID_ARG, "geometry is NULL");
   if (geom->ndim != 2 && geom->ndim != 3) return fail(ctx, WAVE_ERR_INVALID_ARG, "ndim must be 2 or 3");
@@ -469,11 +498,10 @@ int prepare(wave_context* ctx, const wave_geometry* geom, float dt, int nt, int 
   const int ty = (g.NY + step_by(P->R, nd, sp.iso != 0) - 1) / step_by(P->R, nd, sp.iso != 0);
   int chunks = 1;
   if (nd == 3) {
-    const long long tiles = static_cast<long long>(tx) * ty;
-    const long long target = 8LL * 152;
-    chunks = static_cast<int>(std::max<long long>(1, (target + tiles - 1) / tiles));
-    const int min_len = std::max(16, 4 * P->R);
-    chunks = std::min(chunks, std::max(1, g.NZ / min_len));
+    int layout[kStepLayoutMax];
+    const int per_sm = step_layout(P->R, nd, MODE_PLAIN, sp.iso != 0, layout) > 8 ? layout[8] : 2;
+    chunks = choose_chunks(static_cast<long long>(tx) * ty, g.NZ, P->R,
+                           static_cast<long long>(ctx ? ctx->sm_count : 152) * per_sm);
   }
   sp.zchunk = (g.NZ + chunks - 1) / chunks;
   chunks = (g.NZ + sp.zchunk - 1) / sp.zchunk;
@@ -1576,6 +1604,10 @@ int wave_context_create(wave_context** out, int device, size_t hbm_budget_bytes)
     return WAVE_ERR_CUDA;
   }
   ctx->encode = reinterpret_cast<EncodeTiledFn>(fn);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) == cudaSuccess && sms > 0)
+    ctx->sm_count = sms;
+  cudaGetLastError();
   bool ok = cudaMalloc(&ctx->d_status, 16) == cudaSuccess && cudaMalloc(&ctx->d_minmax, 16) == cudaSuccess &&
             cudaMalloc(&ctx->d_phi, 16) == cudaSuccess &&
             cudaMallocHost(&ctx->h_status, 16) == cudaSuccess && cudaMallocHost(&ctx->h_minmax, 16) == cudaSuccess &&
@@ -1789,9 +1821,9 @@ int wave_step_kernel_layout(int space_order, int ndim, int kernel, int equal_spa
   if (!valid_order(space_order) || (ndim != 2 && ndim != 3) || kernel < 0 || kernel >= MODE_COUNT || !out ||
       n_out < 1 || !n_values)
     return WAVE_ERR_INVALID_ARG;
-  int v[16];
+  int v[kStepLayoutMax];
   const int n = step_layout(space_order / 2, ndim, kernel, equal_spacing != 0, v);
-  if (n < 0 || n > 16) return WAVE_ERR_INVALID_ARG;
+  if (n < 0 || n > kStepLayoutMax) return WAVE_ERR_INVALID_ARG;
   for (int i = 0; i < n && i < n_out; ++i) out[i] = v[i];
   *n_values = n;
   return WAVE_OK;

@@ -94,6 +94,8 @@ struct StepTraits {
 template <int R, int NDIM, int MODE, bool ISO = false>
 struct StepLayout {
   using T = StepTraits<R, NDIM, ISO>;
+  static constexpr int HX = T::HX;
+  static constexpr int RZ = T::RZ;
   static constexpr int SNAP_ELEM = mode_snap_fmt(MODE) == 0 ? 4 : 2;
   // per-point tiles loaded with each plane: previous level, cm, and g (the
   // gradient, dm or S) and the snapshot where the mode needs them
@@ -232,7 +234,9 @@ cudaError_t launch_step(int R, int ndim, int mode, const StepMaps& maps, const S
 // Tile geometry of StepTraits<R, NDIM, iso> for the host (maps and grid).
 int step_smem_bytes(int R, int ndim, int mode, bool iso);
 // Compile-time configuration of the step kernel launched for (R, ndim, mode,
-// equal spacing); returns the number of values written to out (at most 16).
+// equal spacing); returns the number of values written to out (at most
+// kStepLayoutMax).
+constexpr int kStepLayoutMax = 32;
 int step_layout(int R, int ndim, int mode, bool iso, int* out);
 int step_bx();
 int step_by(int R, int ndim, bool iso);

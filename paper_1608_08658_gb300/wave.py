@@ -561,9 +561,9 @@ def wave_step_kernel_layout(space_order, ndim, kernel, equal_spacing):
     """Compile-time configuration (dict) of the step kernel launched for these
     arguments; host-only (no GPU needed).  `kernel` is a STEP_KERNELS name or code."""
     k = STEP_KERNELS[kernel] if isinstance(kernel, str) else int(kernel)
-    buf = (ctypes.c_int * 16)()
+    buf = (ctypes.c_int * 32)()
     n = ctypes.c_int()
-    rc = lib().wave_step_kernel_layout(int(space_order), int(ndim), k, int(bool(equal_spacing)), buf, 16,
+    rc = lib().wave_step_kernel_layout(int(space_order), int(ndim), k, int(bool(equal_spacing)), buf, 32,
                                        ctypes.byref(n))
     if rc != WAVE_OK:
         raise WaveError(rc, "bad arguments to wave_step_kernel_layout")
