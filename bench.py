@@ -51,11 +51,12 @@ def parse_args():
     ap.add_argument("--so", type=int, default=8)
     ap.add_argument("--nbl", type=int, default=40)
     ap.add_argument("--snap", default="checkpoint_fp32")
-    ap.add_argument("--mode", default="gradient", choices=["gradient", "forward", "serve", "sweep"],
+    ap.add_argument("--mode", default="gradient", choices=["gradient", "forward", "serve", "sweep", "propagate"],
                     help="gradient: one FWI gradient per step (default); forward: one forward modelling per step; "
                          "serve: a Poisson stream of shot-modelling requests through the continuous-batching server; "
                          "sweep: forward modelling per space order (--orders) on the throughput workload, with the "
-                         "per-launch times of every step-kernel kind")
+                         "per-launch times of every step-kernel kind; propagate: source-free forward modelling of a "
+                         "random initial state, one and two time levels per pass")
     ap.add_argument("--orders", default="2,4,6,8,10,12,14,16", help="sweep mode: space orders")
     ap.add_argument("--kernel-nt", type=int, default=160,
                     help="sweep mode: time levels of the full-storage gradients that time the snapshot and "
@@ -626,6 +627,81 @@ def run_sweep(args, rank, world, local_rank):
     return 0
 
 
+def run_propagate(args, rank, world, local_rank):
+    """Source-free forward modelling (the propagation of a given initial state,
+    wave_forward_ex without sources) on the throughput grid at order --so,
+    timed with one and with two time levels per pass over memory.  The initial
+    state is seeded unit-variance noise; receivers as in the throughput
+    workload.  Point updates per run = points * (nt - 1)."""
+    import torch
+    from paper_1608_08658_gb300 import wave
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w = make_workload(args.n, args.nbl, args.so, args.nt)
+    so, nt = args.so, args.nt
+    geom = wave.Geometry(shape=w["shape"], spacing=w["spacing"], nbl=w["nbl"], sponge_vref=w["vmax"])
+    dt = 0.4 * wave.wave_dt_max(w["spacing"], so, w["vmax"])
+    npts = int(np.prod([s + 2 * w["nbl"] for s in w["shape"]]))
+    m = torch.from_numpy((1.0 / w["v_true"] ** 2).astype(np.float32)).to(dev)
+    rec = torch.from_numpy(w["rec"]).to(dev)
+    g = torch.Generator(device=dev).manual_seed(5)
+    u0 = torch.randn(geom.comp_array_shape, generator=g, device=dev)
+    u1 = torch.randn(geom.comp_array_shape, generator=g, device=dev)
+    d = torch.empty((nt, rec.shape[0]), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    peak, peak_kind = hbm_peak()
+    res = {}
+    launches = 0
+    clocks = ClockSampler() if rank == 0 else None
+    with wave.Context(local_rank) as ctx:
+        for levels in (1, 2):
+            ctx.set_time_blocking(levels)
+            for _ in range(args.warmup):
+                wave.wave_forward(ctx, geom, m, None, None, rec, dt, nt, so, d_out=d, u_init_prev=u0, u_init=u1)
+            torch.cuda.synchronize()
+            ctx.reset_stats()
+            ctx.set_profiling(True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                wave.wave_forward(ctx, geom, m, None, None, rec, dt, nt, so, d_out=d, u_init_prev=u0, u_init=u1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ctx.set_profiling(False)
+            ms = e0.elapsed_time(e1) / args.steps
+            cnt, tms = ctx.kernel_stats(0)
+            launches += ctx.kernel_stats(-1)[0]
+            per_launch = tms / max(1, cnt)
+            upd = levels if (nt - 1) % levels == 0 else None
+            res[levels] = {"ms_per_run": ms, "gpts": npts * (nt - 1) / (ms * 1e-3) / 1e9,
+                           "step_launches": cnt, "ms_per_launch": per_launch,
+                           "bytes_per_update": 16 if levels == 1 else 10,
+                           "achieved_gbs": (16 if levels == 1 else 20) * npts / (per_launch * 1e-3) / 1e9
+                           if upd else None}
+            print("levels per pass %d: %.1f Gpts/s, %.4f ms per step launch" % (levels, res[levels]["gpts"],
+                                                                                per_launch), file=sys.stderr)
+    clk = clocks.stop() if clocks else None
+    if rank == 0:
+        comp = w["shape"][0] + 2 * w["nbl"]
+        ach = res[2]["achieved_gbs"]
+        line = {"metric": METRIC, "value": res[2]["gpts"], "unit": "Gpts/s", "n_gpus": 1, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": res[2]["ms_per_run"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": "3D source-free forward modelling of a random initial state: %d^3 + %d "
+                                       "sponge = %d^3 points, h=10 m, two-layer 1.5/2.5 km/s + 5%% perturbation, "
+                                       "so=%d, nt=%d, %d surface receivers; value with two time levels per pass"
+                                       % (args.n, w["nbl"], comp, so, nt, rec.shape[0]),
+                           "l2": "inputs larger than L2"},
+                "levels": res,
+                "roofline": {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                             "frac": ach / peak if ach else None, "traffic": None, "kernel": "two-level pass",
+                             "bytes_per_point": 20, "points_per_launch": npts,
+                             "peak_source": peak_kind},
+                "gpu_launches": int(launches), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def ctypes_stream(stream):
     import ctypes
     return ctypes.c_void_p(stream.cuda_stream)
@@ -644,6 +720,8 @@ def main():
         return run_serve(args, rank, world, local_rank)
     if args.mode == "sweep":
         return run_sweep(args, rank, world, local_rank)
+    if args.mode == "propagate":
+        return run_propagate(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 

@@ -156,6 +156,19 @@ WAVE_API int wave_context_set_checkpoint_interval(wave_context* ctx, int steps);
  * the limit in force when they are created.  Errors: INVALID_ARG (ctx NULL). */
 WAVE_API int wave_context_set_wait_limit_ns(wave_context* ctx, uint64_t ns);
 
+/* Time levels computed per pass over memory by forward modelling without
+ * sources (wave_forward / wave_forward_ex with an empty source set: the
+ * propagation of a given initial state), at space order 8 in 3D.  levels = 2
+ * fuses two leapfrog levels of Listing 1 / Eq. 1 per pass (temporal blocking,
+ * listed as future work in Sec. VI): 10 bytes of memory traffic per point
+ * update instead of 16, at the price of recomputing the first level on a
+ * halo of R points around each tile; the results equal those of single
+ * levels up to FP32 rounding.  Calls with sources, other orders, 2D grids,
+ * the adjoint, gradient and Born paths always take one level per pass.
+ * levels = 1 (the default) always takes one.  Errors: INVALID_ARG (ctx NULL,
+ * levels not 1 or 2). */
+WAVE_API int wave_context_set_time_blocking(wave_context* ctx, int levels);
+
 /* Test hook of the same failure-detection path (no counterpart in the paper):
  * the context's next stencil-step launch issues none of its tile loads, so
  * every wait of its consumer warps runs out after the wait limit, the kernel

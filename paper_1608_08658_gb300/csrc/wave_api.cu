@@ -75,6 +75,7 @@ struct wave_context {
   int ckpt_interval = 0;
   unsigned long long wait_ns = kWaitLimitNs;  // limit of the step kernels' progress waits
   int sm_count = 152;                         // multiprocessors of the device
+  int time_block = 1;                         // time levels per pass of source-free forward modelling
   bool withhold_next = false;                 // test hook: the next step launch issues no loads
   int last_plan[4] = {0, 0, 0, 0};  // fmt, buffer levels, parts per segment, segments
   // side stream and events that copy finished receiver rows to a pinned host
@@ -901,6 +902,71 @@ int forward_steps(wave_context* ctx, Prob& P, Work& W, int n0, int n1, const flo
   return WAVE_OK;
 }
 
+// Source-free forward modelling with two time levels per pass (step2_kernel):
+// levels rotate through the four field slots, since a pass reads level n with
+// its halo and must write levels n+1 and n+2 elsewhere; an odd last level
+// takes the single-level step.  Receiver rows of both output levels are
+// gathered after each pass.  final_slot receives the slots of levels nt-2 and
+// nt-1.
+int forward_two_level(wave_context* ctx, Prob& P, Work& W, int nt, float* d, PointSetDev* rec, cudaStream_t s,
+                      int* final_slot) {
+  int ex, ey, uw, uh, bx, by;
+  if (step2_box(P.R, &ex, &ey, &uw, &uh, &bx, &by) != 0)
+    return fail(ctx, WAVE_ERR_NOT_SUPPORTED, "two-level pass needs space order 8");
+  const GridDims& g = P.g;
+  StepMaps maps;
+  {
+    cuuint64_t dims[4] = {(cuuint64_t)g.NX, (cuuint64_t)g.NY, (cuuint64_t)g.NZ, 4};
+    cuuint64_t str[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.pitch * g.NY * 4, (cuuint64_t)P.slot_elems * 4};
+    cuuint32_t boxu[4] = {(cuuint32_t)uw, (cuuint32_t)uh, 1, 1};
+    cuuint32_t boxe[4] = {(cuuint32_t)ex, (cuuint32_t)ey, 1, 1};
+    TRY(make_map(ctx, &maps.u, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, W.fields, dims, str, boxu));
+    TRY(make_map(ctx, &maps.p, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, W.fields, dims, str, boxe));
+    cuuint64_t dims3[3] = {(cuuint64_t)g.NX, (cuuint64_t)g.NY, (cuuint64_t)g.NZ};
+    cuuint32_t box3[3] = {(cuuint32_t)ex, (cuuint32_t)ey, 1};
+    TRY(make_map(ctx, &maps.cm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, W.cm, dims3, str, box3));
+    maps.g = maps.cm;
+    maps.s = maps.p;
+  }
+  const int tx = (g.NX + bx - 1) / bx, ty = (g.NY + by - 1) / by;
+  int chunks = choose_chunks(static_cast<long long>(tx) * ty, g.NZ, 2 * P.R, ctx->sm_count);
+  StepParams sp = P.sp;
+  sp.zchunk = (g.NZ + chunks - 1) / chunks;
+  chunks = (g.NZ + sp.zchunk - 1) / sp.zchunk;
+  if (ty > 65535 || chunks > 65535) return fail(ctx, WAVE_ERR_NOT_SUPPORTED, "grid too large for one launch");
+  const dim3 grid(tx, ty, chunks);
+  GatherSet grec = rec ? gather_set(P, rec) : GatherSet{};
+  auto gather = [&](int slot, int row) -> int {
+    if (!rec || rec->n == 0 || !d) return WAVE_OK;
+    float* out = d + static_cast<long long>(row) * rec->n;
+    return launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_gather(grec, slot_ptr(W, P, slot), out, s); });
+  };
+  int s_prev = fslot(-1), s_cur = fslot(0);
+  int n = 0;
+  for (; n + 2 <= nt - 1; n += 2) {
+    int fr[2], k = 0;
+    for (int sl = 0; sl < 4; ++sl)
+      if (sl != s_prev && sl != s_cur) fr[k++] = sl;
+    sp.cur = s_cur;
+    sp.prev = s_prev;
+    sp.out1 = fr[0];
+    sp.out2 = fr[1];
+    TRY(launch(ctx, WAVE_KERNEL_STEP, s, [&] { return launch_step2(P.R, maps, sp, grid, s); }));
+    TRY(gather(fr[0], n + 1));
+    TRY(gather(fr[1], n + 2));
+    s_prev = fr[0];
+    s_cur = fr[1];
+  }
+  if (n < nt - 1) {
+    TRY(step(ctx, P, W, MODE_PLAIN, s_cur, s_prev, s));  // level n+1 overwrites level n-1
+    TRY(gather(s_prev, n + 1));
+    std::swap(s_prev, s_cur);
+  }
+  final_slot[0] = s_prev;
+  final_slot[1] = s_cur;
+  return WAVE_OK;
+}
+
 // Forward steps 0 .. nt-2 with the receiver rows copied to the caller's pinned
 // host buffer in chunks on a side stream, overlapping the copies with the
 // remaining steps; `s` waits for the last copy before the call returns.
@@ -1038,7 +1104,11 @@ int forward_impl(wave_context* ctx, const wave_geometry* geom, const float* m, c
     GatherSet grec = gather_set(P, Rr);
     TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_gather(grec, slot_ptr(W, P, fslot(0)), d, s); }));
   }
-  if (dout.copy_back && dout.pinned) {
+  int final_slot[2] = {fslot(nt - 2), fslot(nt - 1)};
+  if (ctx->time_block == 2 && P.ndim == 3 && P.R == 4 && ns == 0 && nt >= 3) {
+    TRY(forward_two_level(ctx, P, W, nt, d, Rr, s, final_slot));
+    TRY(finish_out(ctx, dout, s));
+  } else if (dout.copy_back && dout.pinned) {
     TRY(forward_steps_streamed(ctx, P, W, nt, static_cast<const float*>(qdev), S, Rr, dout, s));
   } else {
     TRY(forward_steps(ctx, P, W, 0, nt - 1, static_cast<const float*>(qdev), S, d, Rr, nullptr, 0, 0, s));
@@ -1049,7 +1119,7 @@ int forward_impl(wave_context* ctx, const wave_geometry* geom, const float* m, c
     if (!fin) continue;
     OutStage o;
     TRY(stage_out(ctx, k == 0 ? "u_final_prev" : "u_final", fin, P.dense_elems * 4, &o));
-    float* slot = slot_ptr(W, P, fslot(nt - 2 + k));
+    float* slot = slot_ptr(W, P, final_slot[k]);
     TRY(launch(ctx, WAVE_KERNEL_OTHER, s,
                [&] { return launch_pack_state(P.g, slot, static_cast<float*>(o.dev), s); }));
     TRY(finish_out(ctx, o, s));
@@ -1671,6 +1741,12 @@ int wave_context_set_checkpoint_interval(wave_context* ctx, int steps) {
 int wave_context_set_wait_limit_ns(wave_context* ctx, uint64_t ns) {
   if (!ctx) return WAVE_ERR_INVALID_ARG;
   ctx->wait_ns = ns == 0 ? kWaitLimitNs : static_cast<unsigned long long>(ns);
+  return WAVE_OK;
+}
+
+int wave_context_set_time_blocking(wave_context* ctx, int levels) {
+  if (!ctx || (levels != 1 && levels != 2)) return WAVE_ERR_INVALID_ARG;
+  ctx->time_block = levels;
   return WAVE_OK;
 }
 

@@ -217,6 +217,7 @@ struct StepParams {
   int* status;             // device status word
   unsigned long long wait_ns;  // limit of each progress wait (the drain waits keep kWaitLimitNs)
   int withhold;            // test hook: 1 = the producer issues no tile loads (every consumer wait runs out)
+  int out1, out2;          // two-level pass: field slots receiving levels n+1 and n+2
 };
 
 // Host-side launcher for one (R, NDIM, MODE); defined in step_r<R>.cu.
@@ -231,6 +232,13 @@ struct StepMaps {
 // Launches the step kernel variant of p.iso.
 cudaError_t launch_step(int R, int ndim, int mode, const StepMaps& maps, const StepParams& p,
                         dim3 grid, cudaStream_t stream);
+// Two-level pass (step2_kernel.cu): levels n+1 and n+2 of a source-free 3D
+// forward step pair at radius 4 from slots p.prev (n-1) and p.cur (n) into
+// p.out1 and p.out2, which must differ from both.  step2_box gives its tile
+// geometry (extended tile, level-n halo box, output tile); -1 where the pass
+// does not exist.
+cudaError_t launch_step2(int R, const StepMaps& maps, const StepParams& p, dim3 grid, cudaStream_t stream);
+int step2_box(int R, int* ex, int* ey, int* uw, int* uh, int* bx, int* by);
 // Tile geometry of StepTraits<R, NDIM, iso> for the host (maps and grid).
 int step_smem_bytes(int R, int ndim, int mode, bool iso);
 // Compile-time configuration of the step kernel launched for (R, ndim, mode,

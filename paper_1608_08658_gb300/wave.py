@@ -68,6 +68,7 @@ _SIGS = {
     "wave_context_set_checkpoint_interval": (ctypes.c_int, [_P, ctypes.c_int]),
     "wave_context_set_wait_limit_ns": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "wave_context_withhold_next_loads": (ctypes.c_int, [_P]),
+    "wave_context_set_time_blocking": (ctypes.c_int, [_P, ctypes.c_int]),
     "wave_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "wave_last_error": (ctypes.c_char_p, [_P]),
     "wave_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, ctypes.c_int, _P]),
@@ -282,6 +283,10 @@ class Context:
     def set_wait_limit_ns(self, ns):
         """Limit of each bounded wait of the step kernels (0 = the default 10 s)."""
         _check(self, lib().wave_context_set_wait_limit_ns(self.handle, int(ns)))
+
+    def set_time_blocking(self, levels):
+        """Time levels per pass of source-free forward modelling (1 or 2)."""
+        _check(self, lib().wave_context_set_time_blocking(self.handle, int(levels)))
 
     def withhold_next_loads(self):
         """Test hook: the next step launch issues no tile loads (its waits run out)."""
