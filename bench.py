@@ -64,6 +64,9 @@ def parse_args():
     ap.add_argument("--requests", type=int, default=400, help="serve mode: number of requests")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="serve mode: HBM budget for resident requests")
     ap.add_argument("--max-resident", type=int, default=32, help="serve mode: stream slots")
+    ap.add_argument("--batched", action="store_true",
+                    help="serve mode: advance all resident requests together with batched launches")
+    ap.add_argument("--tick-steps", type=int, default=32, help="serve mode, batched: steps per scheduler tick")
     ap.add_argument("--workload", default="throughput", choices=["throughput", "fwi", "paper_demo", "large"],
                     help="throughput: 512^3 two-layer + perturbation (default); fwi: 256^3 + 40, h = 12.5 m, "
                          "v(z) background with Gaussian anomalies, order 8, nt 1500; paper_demo: the paper's 3D "
@@ -487,7 +490,8 @@ def run_serve(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     reqs = inputs.serving_requests(args.requests, seed=99 + rank)
     budget = int(args.budget_gb * (1 << 30))
-    server = serve.ShotServer(device=local_rank, hbm_budget_bytes=budget, max_resident=args.max_resident)
+    server = serve.ShotServer(device=local_rank, hbm_budget_bytes=budget, max_resident=args.max_resident,
+                              batched=args.batched, tick_steps=args.tick_steps)
     # capacity from a burst (all arriving at once) of the first requests
     nb = min(len(reqs), max(8, args.requests // 10))
     burst = server.run(reqs[:nb], np.zeros(nb))
@@ -522,7 +526,9 @@ def run_serve(args, rank, world, local_rank):
                                        "1 Ricker 10 Hz, 100-1000 receivers)" % len(reqs),
                            "arrival_rate_per_s": rate, "burst_capacity_shots_per_s": capacity,
                            "hbm_budget_gb": args.budget_gb, "max_resident": args.max_resident,
-                           "graph_chunk_steps": 32, "l2": "fields of the 3D requests exceed L2"},
+                           "launch_form": ("batched launches, %d steps per tick" % args.tick_steps) if args.batched
+                           else "one stream per request, 32-step graph replays",
+                           "l2": "fields of the 3D requests exceed L2"},
                 "p50_latency_s": summ["p50_latency_s"], "p99_latency_s": summ["p99_latency_s"],
                 "mean_latency_s": summ["mean_latency_s"], "max_resident": summ["max_resident"],
                 "peak_workspace_gb": summ["peak_workspace_bytes"] / 2 ** 30,
@@ -530,7 +536,8 @@ def run_serve(args, rank, world, local_rank):
                 "roofline": None, "cpu_baseline": None,
                 "e2e": {"value": shots, "unit": "shots/s", "h2d_bytes_per_step": int(h2d / len(reqs)),
                         "d2h_bytes_per_step": int(d2h / len(reqs))},
-                "gpu_launches": int(launches), "clocks": clk}
+                "gpu_launches": int(launches), "launches_per_request": launches / max(1, len(stats.results)),
+                "clocks": clk}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

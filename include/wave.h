@@ -315,6 +315,24 @@ WAVE_API int wave_session_create(wave_context* ctx, wave_session** session, cons
  * steps not yet enqueued. */
 WAVE_API int wave_session_advance(wave_session* session, int steps, int* steps_left);
 
+/* Batched advance of several resident sessions (continuous batching of the
+ * serving loop; Listing 1 steps of Eq. 1 for every request): enqueue up to
+ * `steps` more time steps of each of the n sessions on `stream` without
+ * waiting, with one stencil launch per step for all sessions of the same space
+ * order, dimension and spacing variant, and one source-injection and one
+ * receiver-sampling launch per step for all of them.  A session whose steps
+ * run out during the call takes no part in the later launches.  Each session
+ * keeps its own fields, tensor maps and step count, and its results equal
+ * those of wave_session_advance and of wave_forward bit for bit.  All sessions
+ * must share one context; a session must not be advanced on another stream
+ * while this call's work is in flight.  Sessions created with graph_chunk = 0
+ * suit this call (their captured graphs are not used).  The request tables
+ * are staged through a page-locked buffer of the context, which the next call
+ * rewrites only after this call's upload has completed.
+ * Errors: INVALID_ARG (NULL or foreign sessions, n or steps negative); CUDA;
+ * OUT_OF_MEMORY (table workspace beyond the budget). */
+WAVE_API int wave_sessions_advance(wave_session* const* sessions, int n, int steps, void* stream);
+
 /* *done = 1 when every step has been enqueued and has completed. */
 WAVE_API int wave_session_query(wave_session* session, int* done);
 

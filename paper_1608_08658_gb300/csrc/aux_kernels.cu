@@ -99,7 +99,7 @@ __global__ void gather_kernel(GatherSet gs, const float* __restrict__ field, flo
     float w = (bx ? fx : 1.f - fx) * (by ? fy : 1.f - fy);
     if (gs.ndim == 3) w *= (bz ? fz : 1.f - fz);
     const long long idx = gs.base[pt] + bx + by * gs.sy + bz * gs.sz;
-    v = w * field[idx];
+    v = __fmul_rn(w, field[idx]);  // never fused with the reduction below
   }
   for (int off = C / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   if (valid && c == 0) out[pt] = v;
@@ -120,11 +120,12 @@ __global__ void inject_coef_kernel(InjectSet is, GridDims g, const float* __rest
   const long long cell = is.cell[k];
   int x, y, z;
   decode_cell(cell, g, x, y, z);
-  float eta = dev::sponge_term(x, g.NX, g.nblx, emx) + dev::sponge_term(y, g.NY, g.nbly, emy);
-  if (g.NZ > 1) eta += dev::sponge_term(z, g.NZ, g.nblz, emz);
+  // the same operations, in the same order, as the step kernel's damping
+  float eta = dev::sponge_sum(dev::sponge_term(x, g.NX, g.nblx, emx), dev::sponge_term(y, g.NY, g.nbly, emy));
+  if (g.NZ > 1) eta = dev::sponge_sum(eta, dev::sponge_term(z, g.NZ, g.nblz, emz));
   const float c = cm[cell];
-  const float kk = eta * c * half_inv_dt;
-  const float inv = eta == 0.f ? 1.f : __fdividef(1.f, 1.f + kk);  // as in the step kernel
+  const float kk = __fmul_rn(__fmul_rn(eta, c), half_inv_dt);
+  const float inv = eta == 0.f ? 1.f : __fdividef(1.f, __fadd_rn(1.f, kk));
   is.coef[k] = c * inv;
 }
 
@@ -135,7 +136,7 @@ __global__ void inject_kernel(InjectSet is, const float* __restrict__ vals, floa
   if (k >= is.n) return;
   float s = 0.f;
   for (int e = is.rowptr[k]; e < is.rowptr[k + 1]; ++e) s = fmaf(is.w[e], vals[is.pidx[e]], s);
-  field[is.cell[k]] += is.coef[k] * s;
+  field[is.cell[k]] = fmaf(is.coef[k], s, field[is.cell[k]]);
 }
 
 __device__ __forceinline__ float snap_value(const void* snap, int fmt, const float* scale, long long cell,
@@ -304,7 +305,7 @@ __global__ void inject_counter_kernel(InjectSet is, const float* __restrict__ q,
   const float* vals = q + static_cast<long long>(*counter + offset) * ns;
   float s = 0.f;
   for (int e = is.rowptr[k]; e < is.rowptr[k + 1]; ++e) s = fmaf(is.w[e], vals[is.pidx[e]], s);
-  field[is.cell[k]] += is.coef[k] * s;
+  field[is.cell[k]] = fmaf(is.coef[k], s, field[is.cell[k]]);
 }
 
 __global__ void gather_counter_kernel(GatherSet gs, const float* __restrict__ field, float* __restrict__ d,
@@ -320,10 +321,57 @@ __global__ void gather_counter_kernel(GatherSet gs, const float* __restrict__ fi
     const int bx = c & 1, by = (c >> 1) & 1, bz = (c >> 2) & 1;
     float w = (bx ? fx : 1.f - fx) * (by ? fy : 1.f - fy);
     if (gs.ndim == 3) w *= (bz ? fz : 1.f - fz);
-    v = w * field[gs.base[pt] + bx + by * gs.sy + bz * gs.sz];
+    v = __fmul_rn(w, field[gs.base[pt] + bx + by * gs.sy + bz * gs.sz]);
   }
   for (int off = C / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
   if (valid && c == 0) d[static_cast<long long>(*counter + offset) * gs.n + pt] = v;
+}
+
+// Batched injection of the serving path: CTA r injects row n = n0 + k of
+// request r into its level n+1 (the arithmetic of inject_kernel).
+__global__ void inject_batch_kernel(const BatchSparse* __restrict__ table, int k) {
+  const BatchSparse& e = table[blockIdx.x];
+  const int n = e.n0 + k;
+  if (n >= e.nlast || e.inj.n == 0) return;
+  const float* vals = e.q + static_cast<long long>(n) * e.ns;
+  float* field = e.fields + ((n + 1) & 1) * e.slot_elems;
+  for (int c = threadIdx.x; c < e.inj.n; c += blockDim.x) {
+    float s = 0.f;
+    for (int i = e.inj.rowptr[c]; i < e.inj.rowptr[c + 1]; ++i) s = fmaf(e.inj.w[i], vals[e.inj.pidx[i]], s);
+    field[e.inj.cell[c]] = fmaf(e.inj.coef[c], s, field[e.inj.cell[c]]);
+  }
+}
+
+// Batched receiver sampling: the gather CTAs of the requests follow one
+// another (first CTA gcta0); CTA j of request r samples row n + 1 from its
+// level n+1 with the lane layout and reduction of gather_kernel.
+__global__ void gather_batch_kernel(const BatchSparse* __restrict__ table, int nreq, int k) {
+  int lo = 0, hi = nreq - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (table[mid].gcta0 <= static_cast<int>(blockIdx.x)) lo = mid;
+    else hi = mid - 1;
+  }
+  const BatchSparse& e = table[lo];
+  const int n = e.n0 + k;
+  const GatherSet& gs = e.gat;
+  if (n >= e.nlast || gs.n == 0) return;
+  const float* field = e.fields + ((n + 1) & 1) * e.slot_elems;
+  const int C = gs.ndim == 3 ? 8 : 4;
+  const long long t = (static_cast<long long>(blockIdx.x) - e.gcta0) * blockDim.x + threadIdx.x;
+  const long long pt = t / C;
+  const int c = static_cast<int>(t % C);
+  const bool valid = pt < gs.n;
+  float v = 0.f;
+  if (valid) {
+    const float fx = gs.frac[3 * pt], fy = gs.frac[3 * pt + 1], fz = gs.frac[3 * pt + 2];
+    const int bx = c & 1, by = (c >> 1) & 1, bz = (c >> 2) & 1;
+    float w = (bx ? fx : 1.f - fx) * (by ? fy : 1.f - fy);
+    if (gs.ndim == 3) w *= (bz ? fz : 1.f - fz);
+    v = __fmul_rn(w, field[gs.base[pt] + bx + by * gs.sy + bz * gs.sz]);
+  }
+  for (int off = C / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  if (valid && c == 0) e.d[static_cast<long long>(n + 1) * gs.n + pt] = v;
 }
 
 __global__ void counter_add_kernel(int* counter, int delta) {
@@ -387,6 +435,23 @@ cudaError_t launch_inject_grad(const InjectSet& is, const float* values_row, flo
 }
 
 int residual_blocks(long long n) { return blocks_for(n, kThreads, 1024); }
+
+int gather_batch_ctas(long long npoints, int ndim) {
+  const long long lanes = npoints * (ndim == 3 ? 8 : 4);
+  return static_cast<int>((lanes + kThreads - 1) / kThreads);
+}
+
+cudaError_t launch_inject_batch(const BatchSparse* table, int nreq, int k, cudaStream_t s) {
+  if (nreq <= 0) return cudaSuccess;
+  inject_batch_kernel<<<nreq, 64, 0, s>>>(table, k);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_batch(const BatchSparse* table, int nreq, int gather_ctas, int k, cudaStream_t s) {
+  if (nreq <= 0 || gather_ctas <= 0) return cudaSuccess;
+  gather_batch_kernel<<<gather_ctas, kThreads, 0, s>>>(table, nreq, k);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_residual(const float* d, const float* d_obs, float* r, long long n, double* partials,
                             int nblocks, cudaStream_t s) {

@@ -82,10 +82,17 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
 }
 
 // Sponge term of one axis: eta_max/nbl^2 * delta^2, delta = points into the layer.
+// The damping arithmetic (this product, the sum over axes and k = eta cm/(2dt))
+// uses explicitly rounded operations, so no kernel fuses it into an FMA
+// differently from another: every kernel that takes a step (single step,
+// batched step, two-level pass) produces the same bits.
 __device__ __forceinline__ float sponge_term(int i, int n, int nbl, float em_over_nbl2) {
   const int d = max(max(nbl - i, i - (n - 1 - nbl)), 0);
-  return em_over_nbl2 * static_cast<float>(d * d);
+  return __fmul_rn(em_over_nbl2, static_cast<float>(d * d));
 }
+
+// Sum of the sponge terms of two or three axes, in a fixed order.
+__device__ __forceinline__ float sponge_sum(float a, float b) { return __fadd_rn(a, b); }
 
 // Power-of-two slab scale s with amax/s in [2^14, 2^15), built from the
 // exponent field of amax (no rounding involved); 1 for an all-zero slab.

@@ -155,7 +155,10 @@ __global__ void __launch_bounds__(Step2Layout<R>::NTHREADS, 1)
 #pragma unroll
   for (int i = 0; i < 4; ++i) ex[i] = sponge_term(gx + i, p.NX, p.nblx, p.emx);
   const float ey = sponge_term(gy, p.NY, p.nbly, p.emy);
-  const float exy_max = fmaxf(fmaxf(ex[0], ex[1]), fmaxf(ex[2], ex[3])) + ey;
+  float exy[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) exy[i] = sponge_sum(ex[i], ey);
+  const float exy_max = fmaxf(fmaxf(exy[0], exy[1]), fmaxf(exy[2], exy[3]));
 
   float2 cxv[R], cyv[R], czv[R];
 #pragma unroll
@@ -201,7 +204,7 @@ __global__ void __launch_bounds__(Step2Layout<R>::NTHREADS, 1)
   auto update = [&](const float4& c, const float2& la, const float2& lb, const float4& prev, const float4& cm,
                     float ez) -> float4 {
     float4 out;
-    if (exy_max + ez == 0.f) {
+    if (sponge_sum(exy_max, ez) == 0.f) {
       const float2 m1 = make_float2(-1.f, -1.f);
       const float2 ca = make_float2(c.x, c.y), cb = make_float2(c.z, c.w);
       const float2 oa = __ffma2_rn(make_float2(cm.x, cm.y), la,
@@ -211,13 +214,13 @@ __global__ void __launch_bounds__(Step2Layout<R>::NTHREADS, 1)
       out = make_float4(oa.x, oa.y, ob.x, ob.y);
     } else {
       float omk;
-      float inv = damp_inv(ex[0] + ey + ez, cm.x, p.half_inv_dt, omk);
+      float inv = damp_inv(sponge_sum(exy[0], ez), cm.x, p.half_inv_dt, omk);
       out.x = fmaf(cm.x, la.x, fmaf(-omk, prev.x, 2.f * c.x)) * inv;
-      inv = damp_inv(ex[1] + ey + ez, cm.y, p.half_inv_dt, omk);
+      inv = damp_inv(sponge_sum(exy[1], ez), cm.y, p.half_inv_dt, omk);
       out.y = fmaf(cm.y, la.y, fmaf(-omk, prev.y, 2.f * c.y)) * inv;
-      inv = damp_inv(ex[2] + ey + ez, cm.z, p.half_inv_dt, omk);
+      inv = damp_inv(sponge_sum(exy[2], ez), cm.z, p.half_inv_dt, omk);
       out.z = fmaf(cm.z, lb.x, fmaf(-omk, prev.z, 2.f * c.z)) * inv;
-      inv = damp_inv(ex[3] + ey + ez, cm.w, p.half_inv_dt, omk);
+      inv = damp_inv(sponge_sum(exy[3], ez), cm.w, p.half_inv_dt, omk);
       out.w = fmaf(cm.w, lb.y, fmaf(-omk, prev.w, 2.f * c.w)) * inv;
     }
     return out;

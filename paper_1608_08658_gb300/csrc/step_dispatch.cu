@@ -7,7 +7,9 @@ namespace wave {
   cudaError_t launch_step_r##RR(int ndim, int mode, const StepMaps& maps, const StepParams& p, dim3 grid, \
                                 cudaStream_t s);                                                        \
   int step_smem_r##RR(int ndim, int mode, bool iso);                                                    \
-  int step_layout_r##RR(int ndim, int mode, bool iso, int* out);
+  int step_layout_r##RR(int ndim, int mode, bool iso, int* out);                                        \
+  cudaError_t launch_step_batch_r##RR(int ndim, bool iso, const BatchStep* table, int nreq, int ctas, int k,     \
+                                      cudaStream_t s);
 WAVE_DECLARE_RADIUS(1)
 WAVE_DECLARE_RADIUS(2)
 WAVE_DECLARE_RADIUS(3)
@@ -28,6 +30,21 @@ cudaError_t launch_step(int R, int ndim, int mode, const StepMaps& maps, const S
     case 6: return launch_step_r6(ndim, mode, maps, p, grid, stream);
     case 7: return launch_step_r7(ndim, mode, maps, p, grid, stream);
     case 8: return launch_step_r8(ndim, mode, maps, p, grid, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_step_batch(int R, int ndim, bool iso, const BatchStep* table, int nreq, int ctas, int k,
+                              cudaStream_t s) {
+  switch (R) {
+    case 1: return launch_step_batch_r1(ndim, iso, table, nreq, ctas, k, s);
+    case 2: return launch_step_batch_r2(ndim, iso, table, nreq, ctas, k, s);
+    case 3: return launch_step_batch_r3(ndim, iso, table, nreq, ctas, k, s);
+    case 4: return launch_step_batch_r4(ndim, iso, table, nreq, ctas, k, s);
+    case 5: return launch_step_batch_r5(ndim, iso, table, nreq, ctas, k, s);
+    case 6: return launch_step_batch_r6(ndim, iso, table, nreq, ctas, k, s);
+    case 7: return launch_step_batch_r7(ndim, iso, table, nreq, ctas, k, s);
+    case 8: return launch_step_batch_r8(ndim, iso, table, nreq, ctas, k, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -40,9 +40,9 @@ __device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cas
 // reciprocal costs a longer instruction sequence at every sponge point.  The
 // source-injection coefficient uses the same expression.
 __device__ __forceinline__ float damp_inv(float eta, float cm, float half_inv_dt, float& one_minus_k) {
-  const float k = eta * cm * half_inv_dt;
-  one_minus_k = 1.f - k;
-  return eta == 0.f ? 1.f : __fdividef(1.f, 1.f + k);
+  const float k = __fmul_rn(__fmul_rn(eta, cm), half_inv_dt);
+  one_minus_k = __fsub_rn(1.f, k);
+  return eta == 0.f ? 1.f : __fdividef(1.f, __fadd_rn(1.f, k));
 }
 
 template <int FMT>
@@ -172,11 +172,13 @@ __device__ __forceinline__ void produce(const CUtensorMap& tm_u, const CUtensorM
   }
 }
 
+// Body of one step for the CTA at tile (bx, by) and z chunk bz; the step
+// kernel below runs it once per CTA, the batched step of the serving path
+// (step_batch.cu) for the CTAs of several requests.
 template <int R, int NDIM, int MODE, bool ISO>
-__global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayout<R, NDIM, MODE, ISO>::MIN_BLOCKS))
-    step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
-                const __grid_constant__ CUtensorMap tm_cm, const __grid_constant__ CUtensorMap tm_g,
-                const __grid_constant__ CUtensorMap tm_s, const StepParams p) {
+__device__ __forceinline__ void step_body(const CUtensorMap& tm_u, const CUtensorMap& tm_p, const CUtensorMap& tm_cm,
+                                          const CUtensorMap& tm_g, const CUtensorMap& tm_s, const StepParams& p,
+                                          int bx, int by, int bz) {
   using T = StepTraits<R, NDIM, ISO>;
   using L = StepLayout<R, NDIM, MODE, ISO>;
   constexpr int RZ = T::RZ;
@@ -196,9 +198,9 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
   const int tid = threadIdx.x;
   const int warp = tid >> 5;
   const int lane = tid & 31;
-  const int x0 = blockIdx.x * T::BX;
-  const int y0 = blockIdx.y * T::BY;
-  const int z0 = blockIdx.z * p.zchunk;
+  const int x0 = bx * T::BX;
+  const int y0 = by * T::BY;
+  const int z0 = bz * p.zchunk;
   const int z1 = min(z0 + p.zchunk, p.NZ);
   const int nP = z1 - z0;
   const int nU = nP + 2 * RZ;
@@ -239,7 +241,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
   const float ey = sponge_term(gy, p.NY, p.nbly, p.emy);
   float exy[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) exy[i] = sponge_term(gx + i, p.NX, p.nblx, p.emx) + ey;
+  for (int i = 0; i < 4; ++i) exy[i] = sponge_sum(sponge_term(gx + i, p.NX, p.nblx, p.emx), ey);
   // all terms are >= 0: the column is undamped iff the largest is zero
   const float exy_max = fmaxf(fmaxf(exy[0], exy[1]), fmaxf(exy[2], exy[3]));
 
@@ -309,8 +311,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
   const float* scale_ptr = nullptr;
   float scale_next = 1.f;
   if constexpr (mode_is_grad(MODE) && FMT != 0) {
-    scale_ptr = p.scale_in + (static_cast<long long>(z0) * p.slabs_y + (min(gy, p.NY - 1) >> 1)) * p.slabs_x +
-                blockIdx.x;
+    scale_ptr = p.scale_in + (static_cast<long long>(z0) * p.slabs_y + (min(gy, p.NY - 1) >> 1)) * p.slabs_x + bx;
     scale_next = __ldg(scale_ptr);
   }
   float* const out_base = p.fields + p.prev * p.slot_elems;
@@ -441,7 +442,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
     const int gz = z0 + j;
     const float ez = NDIM == 3 ? sponge_term(gz, p.NZ, p.nblz, p.emz) : 0.f;
     float4 out;
-    if (exy_max + ez == 0.f) {
+    if (sponge_sum(exy_max, ez) == 0.f) {
       // undamped: new = 2 cur - prev + cm L (the damped formula at k = 0), on
       // packed pairs
       const float2 m1 = make_float2(-1.f, -1.f);
@@ -453,13 +454,13 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
       out = make_float4(oa.x, oa.y, ob.x, ob.y);
     } else {
       float omk;
-      float inv = damp_inv(exy[0] + ez, cm.x, p.half_inv_dt, omk);
+      float inv = damp_inv(sponge_sum(exy[0], ez), cm.x, p.half_inv_dt, omk);
       out.x = fmaf(cm.x, lap.x, fmaf(-omk, prev.x, 2.f * c.x)) * inv;
-      inv = damp_inv(exy[1] + ez, cm.y, p.half_inv_dt, omk);
+      inv = damp_inv(sponge_sum(exy[1], ez), cm.y, p.half_inv_dt, omk);
       out.y = fmaf(cm.y, lap.y, fmaf(-omk, prev.y, 2.f * c.y)) * inv;
-      inv = damp_inv(exy[2] + ez, cm.z, p.half_inv_dt, omk);
+      inv = damp_inv(sponge_sum(exy[2], ez), cm.z, p.half_inv_dt, omk);
       out.z = fmaf(cm.z, lap.z, fmaf(-omk, prev.z, 2.f * c.z)) * inv;
-      inv = damp_inv(exy[3] + ez, cm.w, p.half_inv_dt, omk);
+      inv = damp_inv(sponge_sum(exy[3], ez), cm.w, p.half_inv_dt, omk);
       out.w = fmaf(cm.w, lap.w, fmaf(-omk, prev.w, 2.f * c.w)) * inv;
     }
     if (store_ok) *reinterpret_cast<float4*>(out_base + idx) = out;
@@ -475,7 +476,7 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
         const float s = slab_scale(amax);
         if (store_ok) store_snap4<FMT>(p.snap_out, idx, c, slab_inv_scale(s));
         if (lane == 0 && gy < p.NY)
-          p.scale_out[(static_cast<long long>(gz) * p.slabs_y + (gy >> 1)) * p.slabs_x + blockIdx.x] = s;
+          p.scale_out[(static_cast<long long>(gz) * p.slabs_y + (gy >> 1)) * p.slabs_x + bx] = s;
       }
     }
     if constexpr (MODE == MODE_BORN_SRC) {
@@ -568,6 +569,14 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
     *abort_flag = 1;
     atomicExch(p.status, kDevTimeout);
   }
+}
+
+template <int R, int NDIM, int MODE, bool ISO>
+__global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayout<R, NDIM, MODE, ISO>::MIN_BLOCKS))
+    step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
+                const __grid_constant__ CUtensorMap tm_cm, const __grid_constant__ CUtensorMap tm_g,
+                const __grid_constant__ CUtensorMap tm_s, const StepParams p) {
+  step_body<R, NDIM, MODE, ISO>(tm_u, tm_p, tm_cm, tm_g, tm_s, p, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace dev

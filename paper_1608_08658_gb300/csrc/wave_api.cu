@@ -82,6 +82,11 @@ struct wave_context {
   // buffer while later time steps run (created on first use)
   cudaStream_t copy_stream = nullptr;
   cudaEvent_t ev_rows = nullptr, ev_copied = nullptr, ev_input = nullptr;
+  // page-locked staging of the request tables of batched session steps, and
+  // the event after their last upload (the buffer is rewritten only after it)
+  void* batch_host = nullptr;
+  size_t batch_cap = 0;
+  cudaEvent_t ev_batch = nullptr;
 };
 
 namespace {
@@ -1713,6 +1718,8 @@ int wave_context_destroy(wave_context* ctx) {
   if (ctx->ev_copied) cudaEventDestroy(ctx->ev_copied);
   if (ctx->ev_input) cudaEventDestroy(ctx->ev_input);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
+  if (ctx->ev_batch) cudaEventDestroy(ctx->ev_batch);
   cudaGetLastError();
   delete ctx;
   return WAVE_OK;
@@ -2001,6 +2008,121 @@ int wave_session_advance(wave_session* S, int steps, int* steps_left) {
   return WAVE_OK;
 }
 
+int wave_sessions_advance(wave_session* const* sessions, int n, int steps, void* stream) {
+  if (n < 0 || steps < 0 || (n > 0 && !sessions)) return WAVE_ERR_INVALID_ARG;
+  if (n == 0 || steps == 0) return WAVE_OK;
+  if (!sessions[0]) return WAVE_ERR_INVALID_ARG;
+  wave_context* ctx = sessions[0]->ctx;
+  for (int i = 0; i < n; ++i)
+    if (!sessions[i] || sessions[i]->ctx != ctx)
+      return fail(ctx, WAVE_ERR_INVALID_ARG, "sessions must be non-NULL and share one context");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // this call's steps of every session, and its groups (radius, dimension,
+  // spacing variant: one batched step launch per group and step)
+  struct Item {
+    wave_session* S;
+    int n0, nlast;
+  };
+  std::vector<Item> items;
+  int kmax = 0;
+  for (int i = 0; i < n; ++i) {
+    wave_session* S = sessions[i];
+    const int total = S->P.nt - 1;
+    const int take = std::min(steps, total - S->next);
+    if (take <= 0) continue;
+    items.push_back({S, S->next, S->next + take});
+    kmax = std::max(kmax, take);
+  }
+  if (items.empty()) return WAVE_OK;
+  std::map<int, std::vector<int>> groups;
+  for (int i = 0; i < static_cast<int>(items.size()); ++i) {
+    const Prob& P = items[i].S->P;
+    groups[(P.R * 4 + P.ndim) * 2 + P.sp.iso].push_back(i);
+  }
+  const size_t step_bytes = sizeof(BatchStep) * items.size();
+  const size_t sparse_off = round_up(step_bytes, 256);
+  const size_t bytes = sparse_off + sizeof(BatchSparse) * items.size();
+  if (ctx->ev_batch) CK(cudaEventSynchronize(ctx->ev_batch));  // the previous upload has read the staging
+  if (bytes > ctx->batch_cap) {
+    if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
+    ctx->batch_host = nullptr;
+    ctx->batch_cap = 0;
+    CK(cudaMallocHost(&ctx->batch_host, bytes));
+    ctx->batch_cap = bytes;
+  }
+  if (!ctx->ev_batch) CK(cudaEventCreateWithFlags(&ctx->ev_batch, cudaEventDisableTiming));
+  unsigned char* host = static_cast<unsigned char*>(ctx->batch_host);
+  BatchStep* hstep = reinterpret_cast<BatchStep*>(host);
+  BatchSparse* hsparse = reinterpret_cast<BatchSparse*>(host + sparse_off);
+  struct Group {
+    int R, ndim;
+    bool iso;
+    int first, count, ctas;
+  };
+  std::vector<Group> glist;
+  int e = 0;
+  bool any_src = false, any_rec = false;
+  for (auto& kv : groups) {
+    const Prob& P0 = items[kv.second[0]].S->P;
+    Group gr{P0.R, P0.ndim, P0.sp.iso != 0, e, 0, 0};
+    for (int i : kv.second) {
+      const Item& it = items[i];
+      const Prob& P = it.S->P;
+      BatchStep& b = hstep[e++];
+      b.maps = it.S->W.maps;
+      b.p = P.sp;
+      b.cta0 = gr.ctas;
+      b.tiles_x = static_cast<int>(P.grid.x);
+      b.tiles_y = static_cast<int>(P.grid.y);
+      b.n0 = it.n0;
+      b.nlast = it.nlast;
+      gr.ctas += static_cast<int>(P.grid.x * P.grid.y * P.grid.z);
+      gr.count++;
+    }
+    glist.push_back(gr);
+  }
+  int gctas = 0;
+  for (int i = 0; i < static_cast<int>(items.size()); ++i) {
+    wave_session* S = items[i].S;
+    BatchSparse& b = hsparse[i];
+    b.inj = inject_set(&S->src);
+    b.q = S->q;
+    b.ns = S->ns;
+    b.gat = gather_set(S->P, &S->rec);
+    b.d = S->d;
+    b.fields = S->W.fields;
+    b.slot_elems = S->P.slot_elems;
+    b.n0 = items[i].n0;
+    b.nlast = items[i].nlast;
+    b.gcta0 = gctas;
+    gctas += gather_batch_ctas(S->nr, S->P.ndim);
+    any_src = any_src || S->src.ncell > 0;
+    any_rec = any_rec || S->nr > 0;
+  }
+  void* dev = nullptr;
+  TRY(ws_get(ctx, "batch_table", bytes, &dev));
+  CK(cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, s));
+  CK(cudaEventRecord(ctx->ev_batch, s));
+  const BatchStep* dstep = static_cast<const BatchStep*>(dev);
+  const BatchSparse* dsparse = reinterpret_cast<const BatchSparse*>(static_cast<unsigned char*>(dev) + sparse_off);
+  const int nitems = static_cast<int>(items.size());
+  for (int k = 0; k < kmax; ++k) {
+    for (const Group& gr : glist)
+      TRY(launch(ctx, WAVE_KERNEL_STEP, s, [&] {
+        return launch_step_batch(gr.R, gr.ndim, gr.iso, dstep + gr.first, gr.count, gr.ctas, k, s);
+      }));
+    if (any_src) TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_inject_batch(dsparse, nitems, k, s); }));
+    if (any_rec)
+      TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_gather_batch(dsparse, nitems, gctas, k, s); }));
+  }
+  for (const Item& it : items) {
+    it.S->next = it.nlast;
+    if (it.S->next >= it.S->P.nt - 1) CK(cudaEventRecord(it.S->done, s));
+  }
+  return WAVE_OK;
+}
+
 int wave_session_query(wave_session* S, int* done) {
   if (!S || !done) return WAVE_ERR_INVALID_ARG;
   *done = 0;
@@ -2020,6 +2142,8 @@ int wave_session_read(wave_session* S, float* d_out) {
   if (S->next < S->P.nt - 1) return fail(ctx, WAVE_ERR_INVALID_ARG, "session has steps left to enqueue");
   DeviceGuard guard(ctx->device);
   if (S->nr > 0 && !d_out) return fail(ctx, WAVE_ERR_INVALID_ARG, "output is NULL");
+  // the last steps may have been enqueued on another stream (batched advance)
+  CK(cudaStreamWaitEvent(S->stream, S->done, 0));
   if (S->nr > 0)
     CK(cudaMemcpyAsync(d_out, S->d, static_cast<size_t>(S->P.nt) * S->nr * 4, cudaMemcpyDefault, S->stream));
   CK(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, S->stream));
@@ -2032,6 +2156,7 @@ int wave_session_destroy(wave_session* S) {
   if (!S) return WAVE_OK;
   DeviceGuard guard(S->ctx->device);
   cudaStreamSynchronize(S->stream);
+  if (S->done && S->next > 0) cudaEventSynchronize(S->done);  // steps enqueued on another stream
   if (S->exec) cudaGraphExecDestroy(S->exec);
   if (S->done) cudaEventDestroy(S->done);
   sess_free(S);

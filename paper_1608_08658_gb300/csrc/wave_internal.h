@@ -229,6 +229,17 @@ struct StepMaps {
   CUtensorMap s;   // snapshot store, tile box (4D: x, y, z, level)
 };
 
+// One resident request of a batched step launch (serving): the CTAs
+// [cta0, cta0 + tiles_x * tiles_y * chunks) of the launch run the request's
+// step n0 + k (k: the launch's index within the call) while n0 + k < nlast.
+// Lives in device memory; the tensor maps are read from there.
+struct alignas(64) BatchStep {
+  StepMaps maps;
+  StepParams p;
+  int cta0;
+  int tiles_x, tiles_y;
+  int n0, nlast;
+};
 // Launches the step kernel variant of p.iso.
 cudaError_t launch_step(int R, int ndim, int mode, const StepMaps& maps, const StepParams& p,
                         dim3 grid, cudaStream_t stream);
@@ -239,6 +250,10 @@ cudaError_t launch_step(int R, int ndim, int mode, const StepMaps& maps, const S
 // does not exist.
 cudaError_t launch_step2(int R, const StepMaps& maps, const StepParams& p, dim3 grid, cudaStream_t stream);
 int step2_box(int R, int* ex, int* ey, int* uw, int* uh, int* bx, int* by);
+// Batched plain step of nreq requests sharing (R, ndim, iso): `ctas` CTAs in
+// all, table in device memory; launch index k within the call.
+cudaError_t launch_step_batch(int R, int ndim, bool iso, const BatchStep* table, int nreq, int ctas, int k,
+                              cudaStream_t stream);
 // Tile geometry of StepTraits<R, NDIM, iso> for the host (maps and grid).
 int step_smem_bytes(int R, int ndim, int mode, bool iso);
 // Compile-time configuration of the step kernel launched for (R, ndim, mode,
@@ -278,6 +293,20 @@ struct InjectSet {
   const float* w;          // weight per entry
   float* coef;             // per cell cm/(1+k), filled by launch_inject_coef
 };
+// Source injection and receiver sampling of one request in a batched launch
+// (step n = n0 + k: injection of row n into level n+1, gather of row n+1).
+struct BatchSparse {
+  InjectSet inj;
+  const float* q;          // [nt][ns]
+  long long ns;
+  GatherSet gat;
+  float* d;                // [nt][nr]
+  float* fields;           // the request's two field slots
+  long long slot_elems;
+  int n0, nlast;
+  int gcta0;               // first CTA of the request's gather in the launch
+};
+
 cudaError_t launch_gather(const GatherSet& gs, const float* field, float* out_row, cudaStream_t s);
 cudaError_t launch_inject_coef(const InjectSet& is, const GridDims& g, const float* cm,
                                const float* eta_max_over_nbl2, float half_inv_dt, cudaStream_t s);
@@ -306,5 +335,10 @@ cudaError_t launch_inject_counter(const InjectSet& is, const float* q, long long
 cudaError_t launch_gather_counter(const GatherSet& gs, const float* field, float* d, const int* counter, int offset,
                                   cudaStream_t s);
 cudaError_t launch_counter_add(int* counter, int delta, cudaStream_t s);
+// batched injection (one CTA per request) and receiver sampling (gather CTAs
+// of the requests one after another, gather_ctas in all) of launch index k
+cudaError_t launch_inject_batch(const BatchSparse* table, int nreq, int k, cudaStream_t s);
+cudaError_t launch_gather_batch(const BatchSparse* table, int nreq, int gather_ctas, int k, cudaStream_t s);
+int gather_batch_ctas(long long npoints, int ndim);
 
 }  // namespace wave

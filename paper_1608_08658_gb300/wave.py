@@ -100,6 +100,7 @@ _SIGS = {
                                            ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
     "wave_session_advance": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "wave_session_query": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "wave_sessions_advance": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int, _P]),
     "wave_session_read": (ctypes.c_int, [_P, _P]),
     "wave_session_destroy": (ctypes.c_int, [_P]),
     "wave_context_budget_free": (ctypes.c_size_t, [_P]),
@@ -363,6 +364,22 @@ class Session:
             self.close()
         except Exception:  # noqa: BLE001 - interpreter shutdown
             pass
+
+
+def wave_sessions_advance(sessions, steps, stream=None):
+    """Enqueue up to ``steps`` more steps of every session in ``sessions`` with
+    batched launches (one stencil launch per step per space order, dimension and
+    spacing variant; one injection and one receiver launch per step) on
+    ``stream`` (a ctypes c_void_p or None)."""
+    sessions = list(sessions)
+    if not sessions:
+        return
+    arr = (ctypes.c_void_p * len(sessions))(*[sess.handle for sess in sessions])
+    rc = lib().wave_sessions_advance(arr, len(sessions), int(steps), stream)
+    if rc != WAVE_OK:
+        raise WaveError(rc, lib().wave_last_error(sessions[0].ctx.handle).decode())
+    for sess in sessions:
+        sess.steps_left = max(0, sess.steps_left - int(steps))
 
 
 def wave_session_footprint(ctx, geom, src, rec, nt, space_order):

@@ -57,12 +57,16 @@ def test_session_equals_forward(ctx, chunk):
         np.testing.assert_array_equal(got, _alone(ctx, req))
 
 
-def test_results_alone_equal_results_in_the_mix(ctx):
+@pytest.mark.parametrize("batched", [False, True])
+def test_results_alone_equal_results_in_the_mix(ctx, batched):
+    """batched: the 2D requests (up to 60 000 points here) advance together by
+    batched launches, the 3D ones on stream slots."""
     reqs = _small_requests(12)
     geoms = [request_problem(r, torch.device("cuda", 0)) for r in reqs]
     fps = [wave.wave_session_footprint(ctx, g[0], g[2], g[4], r["nt"], r["so"]) for g, r in zip(geoms, reqs)]
     budget = int(2.5 * max(fps)) + (64 << 20)
-    server = ShotServer(device=0, hbm_budget_bytes=budget, max_resident=5)
+    server = ShotServer(device=0, hbm_budget_bytes=budget, max_resident=5, batched=batched, tick_steps=16,
+                        batch_max_points=60_000)
     try:
         arrivals = np.sort(inputs.rng(4).uniform(0.0, 0.3, size=len(reqs)))
         stats = server.run(reqs, arrivals)
@@ -74,5 +78,52 @@ def test_results_alone_equal_results_in_the_mix(ctx):
     for r in reqs:
         np.testing.assert_array_equal(stats.results[r["id"]].data, _alone(ctx, r))
     s = stats.summary()
-    print("served %d requests: %.1f shots/s, p50 %.3f s, p99 %.3f s, max resident %d"
-          % (s["requests"], s["shots_per_s"], s["p50_latency_s"], s["p99_latency_s"], s["max_resident"]))
+    print("served %d requests%s: %.1f shots/s, p50 %.3f s, p99 %.3f s, max resident %d"
+          % (s["requests"], " (small ones batched)" if batched else "", s["shots_per_s"], s["p50_latency_s"],
+             s["p99_latency_s"], s["max_resident"]))
+
+
+def test_batched_advance_equals_forward(ctx):
+    """Sessions of mixed dimension and order advanced together by batched
+    launches (three of them join after the first call; 23 steps per call, not
+    a divisor of any nt) return what wave_forward returns for each alone, bit
+    for bit, with far fewer launches than advancing them one by one."""
+    reqs = _small_requests(8, seed=21)
+    dev = torch.device("cuda", 0)
+    batch_stream, setup_stream = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    bs = wave.ctypes.c_void_p(batch_stream.cuda_stream)
+    ss = wave.ctypes.c_void_p(setup_stream.cuda_stream)
+    sess = []
+    for r in reqs:
+        geom, m, src, q, rec, dt = request_problem(r, dev)
+        torch.cuda.synchronize()
+        sess.append(wave.Session(ctx, geom, m, src, q, rec, dt, r["nt"], r["so"], stream=ss, graph_chunk=0))
+    ctx.reset_stats()
+    wave.wave_sessions_advance(sess[:5], 23, bs)
+    while any(s.steps_left > 0 for s in sess):
+        wave.wave_sessions_advance([s for s in sess if s.steps_left > 0], 23, bs)
+    launches = ctx.kernel_stats(-1)[0]
+    batch_stream.synchronize()
+    for s, r in zip(sess, reqs):
+        assert s.done()
+        got = s.read()
+        s.close()
+        np.testing.assert_array_equal(got, _alone(ctx, r))
+    one_by_one = sum(3 * (r["nt"] - 1) for r in reqs)
+    print("batched advance: %d launches for %d requests (%d one by one)" % (launches, len(reqs), one_by_one))
+    assert launches < one_by_one / 2
+
+
+def test_batched_advance_rejects_foreign_sessions(ctx):
+    reqs = _small_requests(2, seed=5)
+    dev = torch.device("cuda", 0)
+    with wave.Context(0) as other:
+        g0, m0, s0, q0, r0, dt0 = request_problem(reqs[0], dev)
+        g1, m1, s1, q1, r1, dt1 = request_problem(reqs[1], dev)
+        a = wave.Session(ctx, g0, m0, s0, q0, r0, dt0, reqs[0]["nt"], reqs[0]["so"], graph_chunk=0)
+        b = wave.Session(other, g1, m1, s1, q1, r1, dt1, reqs[1]["nt"], reqs[1]["so"], graph_chunk=0)
+        with pytest.raises(wave.WaveError) as e:
+            wave.wave_sessions_advance([a, b], 5)
+        assert e.value.code == wave.WAVE_ERR_INVALID_ARG
+        a.close()
+        b.close()
