@@ -50,6 +50,7 @@ struct Step2Layout {
   static constexpr int U_BYTES = UW * UH * 4;
   static constexpr int U_STRIDE = (U_BYTES + 127) / 128 * 128;
   static constexpr bool LEAD = true;
+  static constexpr bool COMBINED = false;  // separate queue-feed and per-point barriers
   static constexpr int PF = 3;
   static constexpr int NSU = PF + 1;
   static constexpr int NSP = PF + 1;

@@ -123,8 +123,46 @@ __device__ __forceinline__ void produce(const CUtensorMap& tm_u, const CUtensorM
   prefetch_tensormap(&tm_cm);
   if (mode_loads_g(MODE)) prefetch_tensormap(&tm_g);
   if (mode_is_grad(MODE)) prefetch_tensormap(&tm_s);
-  int issuedU = 0, issuedP = 0;
   bool ok = true;
+  if constexpr (L::COMBINED) {
+    // one ring: stage s = queue box of plane z0 - RZ + s plus, from s = 2RZ
+    // on, the per-point tiles of plane s - 2RZ, under fullU/emptyU[s % NSU]
+    constexpr int NS = L::NSU;
+    static_assert(L::NSU == L::NSP, "one stage per plane for both rings");
+    int issued = 0;
+    for (int s = 0; s < nU; ++s) {
+      const int slot = s % NS;
+      if (s >= NS) ok = mbar_wait_bounded(&emptyU[slot], ((s / NS) - 1) & 1, abort_flag, p.wait_ns);
+      if (!ok) break;
+      const bool tiles = s >= 2 * RZ;
+      mbar_arrive_expect_tx(&fullU[slot], L::Q_BYTES + (tiles ? L::P_TX : 0));
+      tma_load_4d(Ubase + slot * (L::Q_STRIDE / 4), &tm_p, x0, y0, z0 - RZ + s, p.cur, &fullU[slot]);
+      if (tiles) {
+        const int j = s - 2 * RZ;
+        unsigned char* pd = Pbase + slot * L::P_BYTES;
+        tma_load_4d(pd + L::HALO_OFF, &tm_u, x0 - L::HX, y0 - R, z0 + j, p.cur, &fullU[slot]);
+        tma_load_4d(pd + L::PREV_OFF, &tm_p, x0, y0, z0 + j, p.prev, &fullU[slot]);
+        tma_load_3d(pd + L::CM_OFF, &tm_cm, x0, y0, z0 + j, &fullU[slot]);
+        if (mode_loads_g(MODE)) tma_load_3d(pd + L::G_OFF, &tm_g, x0, y0, z0 + j, &fullU[slot]);
+        if (mode_is_grad(MODE)) tma_load_4d(pd + L::S_OFF, &tm_s, x0, y0, z0 + j, p.snap_level, &fullU[slot]);
+      }
+      issued = s + 1;
+    }
+    if (!ok) {
+      *abort_flag = 1;
+      atomicExch(p.status, kDevTimeout);
+    }
+    if (*abort_flag) {
+      for (int slot = 0; slot < NS; ++slot) {
+        if (issued > slot) {
+          const int last = slot + NS * ((issued - 1 - slot) / NS);
+          mbar_wait_bounded(&fullU[slot], (last / NS) & 1, nullptr, kWaitLimitNs);
+        }
+      }
+    }
+    return;
+  }
+  int issuedU = 0, issuedP = 0;
   for (int s = 0; s < nU; ++s) {
     const int slot = s % L::NSU;
     if (s >= L::NSU) ok = mbar_wait_bounded(&emptyU[slot], ((s / L::NSU) - 1) & 1, abort_flag, p.wait_ns);
@@ -323,23 +361,24 @@ __device__ __forceinline__ void step_body(const CUtensorMap& tm_u, const CUtenso
 
   // One output plane z = z0 + j, taking its queue entries at offset O of a
   // window renamed by PH (entry i at q[(PH + O + i) % NQ]).
-  auto plane = [&](auto oc, auto phc) -> bool {
+  // un / pu: queue-feed stage and phase of the plane; ps / pp: its per-point
+  // stage and phase (the same stage in the one-ring layout)
+  auto plane = [&](auto oc, auto phc, int un, uint32_t pu, int ps, uint32_t pp) -> bool {
     constexpr int O = decltype(oc)::value;
     constexpr int PH = decltype(phc)::value;
     auto qi = [](int i) { return (PH + O + i) % NQ; };
-    const int un = ring_un, ps = ring_ps;
     const int uc = un >= RZ ? un - RZ : un + L::NSU - RZ;  // slot of the centre plane
-    bool good = mbar_wait_bounded(&fullU[un], phase_un, abort_flag, p.wait_ns);
+    bool good = mbar_wait_bounded(&fullU[un], pu, abort_flag, p.wait_ns);
     if (!__all_sync(0xffffffffu, good)) return false;
     q[qi(2 * RZ)] = lds4(Ubase + un * (L::Q_STRIDE / 4) + qofs);
-    if constexpr (L::LEAD) {
+    if constexpr (L::LEAD && !L::COMBINED) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&emptyU[un]);
     }
     const float4 c = q[qi(RZ)];
-    if constexpr (L::LEAD) {
+    if constexpr (L::LEAD && !L::COMBINED) {
       // the centre halo box arrives with the per-point tiles
-      good = mbar_wait_bounded(&fullP[ps], phase_ps, abort_flag, p.wait_ns);
+      good = mbar_wait_bounded(&fullP[ps], pp, abort_flag, p.wait_ns);
       if (!__all_sync(0xffffffffu, good)) return false;
     }
     const float* Uc = L::LEAD ? reinterpret_cast<const float*>(Pbase + ps * L::P_BYTES + L::HALO_OFF) + lofs
@@ -425,7 +464,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap& tm_u, const CUtenso
       }
     }
     if constexpr (!L::LEAD) {
-      good = mbar_wait_bounded(&fullP[ps], phase_ps, abort_flag, p.wait_ns);
+      good = mbar_wait_bounded(&fullP[ps], pp, abort_flag, p.wait_ns);
       if (!__all_sync(0xffffffffu, good)) return false;
     }
     const unsigned char* Pst = Pbase + ps * L::P_BYTES;
@@ -507,10 +546,19 @@ __device__ __forceinline__ void step_body(const CUtensorMap& tm_u, const CUtenso
 
     __syncwarp();
     if (lane == 0) {
-      if constexpr (!L::LEAD) mbar_arrive(&emptyU[uc]);
-      mbar_arrive(&emptyP[ps]);
+      if constexpr (L::COMBINED) {
+        mbar_arrive(&emptyU[un]);
+      } else {
+        if constexpr (!L::LEAD) mbar_arrive(&emptyU[uc]);
+        mbar_arrive(&emptyP[ps]);
+      }
     }
     return true;
+  };
+  // the plane at the runtime ring positions
+  auto ring = [&](auto oc, auto phc) -> bool {
+    if constexpr (L::COMBINED) return plane(oc, phc, ring_un, phase_un, ring_un, phase_un);
+    else return plane(oc, phc, ring_un, phase_un, ring_ps, phase_ps);
   };
 
   // ring slots and phases advance by one per plane (no division in the loop)
@@ -528,19 +576,47 @@ __device__ __forceinline__ void step_body(const CUtensorMap& tm_u, const CUtenso
   };
   if (ok && QU == 2) {
     while (j + 2 <= nP) {
-      ok = plane(IntC<0>{}, IntC<0>{});
+      ok = ring(IntC<0>{}, IntC<0>{});
       if (!ok) break;
       advance();
-      ok = plane(IntC<QU - 1>{}, IntC<0>{});
+      ok = ring(IntC<QU - 1>{}, IntC<0>{});
       if (!ok) break;
       advance();
 #pragma unroll
       for (int i = 0; i < 2 * RZ; ++i) q[i] = q[i + QU];
     }
   }
-  if constexpr (UR > 1) {
+  if constexpr (UR > 1 && L::COMBINED && UR == L::NSU) {
+    // groups of NSU planes from j = 0: plane u of a group uses stage
+    // (2RZ + u) % NSU, whose phase is the group's parity flipped by
+    // (2RZ + u) / NSU -- both known at compile time but for the parity
+    uint32_t gpar = 0;
     auto renamed = [&](auto phc) -> bool {
-      if (!plane(IntC<0>{}, phc)) return false;
+      constexpr int u = decltype(phc)::value;
+      constexpr int sl = (2 * RZ + u) % L::NSU;
+      const uint32_t par = gpar ^ static_cast<uint32_t>(((2 * RZ + u) / L::NSU) & 1);
+      if (!plane(IntC<0>{}, phc, sl, par, sl, par)) return false;
+      ++j;
+      idx += plane_elems;
+      return true;
+    };
+    while (ok && j + UR <= nP) {
+      ok = call_in_order(renamed, IntC<0>{}, IntC<UR>{});
+      if (!ok) break;
+      gpar ^= 1u;
+      if constexpr (UR % NQ != 0) {
+        float4 t[NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) t[i] = q[(i + UR) % NQ];
+#pragma unroll
+        for (int i = 0; i < NQ; ++i) q[i] = t[i];
+      }
+    }
+    ring_un = (j + 2 * RZ) % L::NSU;
+    phase_un = ((j + 2 * RZ) / L::NSU) & 1;
+  } else if constexpr (UR > 1) {
+    auto renamed = [&](auto phc) -> bool {
+      if (!ring(IntC<0>{}, phc)) return false;
       advance();
       return true;
     };
@@ -558,7 +634,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap& tm_u, const CUtenso
   }
   if (ok) {
     while (j < nP) {
-      ok = plane(IntC<0>{}, IntC<0>{});
+      ok = ring(IntC<0>{}, IntC<0>{});
       if (!ok) break;
       advance();
 #pragma unroll

@@ -161,12 +161,20 @@ struct StepLayout {
   //    16-bit snapshot, imaging and Born steps at radius 6, general spacing
   //    from radius 7) and for the paired planes of the deep steps up to
   //    radius 2 (no measurable difference there).
-  static constexpr int UR =
+  static constexpr int UR_BASE =
       (NDIM != 3 || QU != 1) ? 1
       : (R >= kLeadMinR) ? (ISO ? kRenameGroup : 1)
       : ((R == 5 && mode_is_grad(MODE)) || (R == 6 && MODE >= MODE_SNAP_BF16)) ? 1
       : ((DEEP && (R == 3 || R == 4)) || (R == 4 && MODE == MODE_GRAD_F32)) ? 2 * R + 1
       : kRenameGroup;
+  // Lead-plane layouts take one stage per plane for both rings: stage s holds
+  // the queue box of plane z0 - RZ + s and, from s = 2RZ on, the per-point
+  // tiles of plane s - 2RZ, under one full and one empty barrier (one wait and
+  // one release per plane).  Their renamed groups span exactly the NSU stages,
+  // so that within a group every stage slot is a compile-time offset and the
+  // phase flips once per group.
+  static constexpr bool COMBINED = LEAD;
+  static constexpr int UR = (COMBINED && UR_BASE > 1) ? nsu_of(LEAD, PF) : UR_BASE;
   // resident CTAs per SM asked of the register allocator (registers per
   // thread follow the warps per SM sub-partition: 3 CTAs of 9 warps leave 72,
   // 2 of 9 leave 96, 2 of 8 leave 128)
