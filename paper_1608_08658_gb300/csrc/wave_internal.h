@@ -118,9 +118,18 @@ struct StepLayout {
   }
   static constexpr bool fits(bool lead, int pf, int nsp) { return smem_of(lead, pf, nsp) <= kSmemTwoCtas; }
 
-  // Lead-plane design from radius 7 on, and wherever the classic design would
-  // not fit two CTAs per SM.
-  static constexpr bool LEAD = (NDIM == 3) && (R >= kLeadMinR || !fits(false, 2, 3));
+  // Lead-plane design from radius 7 on for every step; from radius 3 for the
+  // plain and 16-bit-snapshot steps and from radius 5 for the FP32-snapshot
+  // and 16-bit imaging steps, where it was measured faster on 592^3 (order 8
+  // plain step 0.530 -> 0.519 ms, order 10 FP32 snapshot 0.663 -> 0.647 ms,
+  // order 10 FP16 imaging 0.886 -> 0.847 ms; the FP32 snapshot and imaging
+  // steps up to radius 4 were slower: 0.640 -> 0.658 and 0.854 -> 0.883 ms at
+  // order 8); and wherever the classic design would not fit two CTAs per SM.
+  static constexpr bool LEAD_PREFERRED =
+      R >= kLeadMinR ||
+      (R >= 3 && (MODE == MODE_PLAIN || MODE == MODE_SNAP_BF16 || MODE == MODE_SNAP_F16)) ||
+      (R >= 5 && (MODE == MODE_SNAP_F32 || MODE == MODE_GRAD_BF16 || MODE == MODE_GRAD_F16));
+  static constexpr bool LEAD = (NDIM == 3) && (LEAD_PREFERRED || !fits(false, 2, 3));
   // Deep variant (classic design, not the imaging condition): two CTAs per SM
   // with a 4-plane prefetch (3 where 4 would not fit two CTAs) and, up to
   // radius 2, output planes taken in pairs (half the register-queue moves),
@@ -138,7 +147,7 @@ struct StepLayout {
   // order 16 forward 0.838 -> 0.827 ms, snapshot 0.884 -> 0.860 ms, FP32
   // imaging 0.982 -> 0.964 ms on 592^3.
   static constexpr int LEAD_PF =
-      (NDIM == 3 && LEAD && R >= kLeadMinR) ? (fits(true, 4, 5) ? 4 : (fits(true, 3, 4) ? 3 : 0)) : 0;
+      (NDIM == 3 && LEAD && LEAD_PREFERRED) ? (fits(true, 4, 5) ? 4 : (fits(true, 3, 4) ? 3 : 0)) : 0;
   static constexpr int PF =
       NDIM == 3 ? (DEEP ? DEEP_PF : (LEAD_PF > 0 ? LEAD_PF : (G16_DEEP ? 3 : 2))) : 0;  // planes prefetched ahead
   static constexpr int NSP =
