@@ -72,6 +72,9 @@ def parse_args():
                          "v(z) background with Gaussian anomalies, order 8, nt 1500; paper_demo: the paper's 3D "
                          "demonstration shape 201x201x70 + 40 (h = 15 m, order 14, 1 s, 10 Hz); large: "
                          "1000x1000x600 + 40, order 16, layered model with a salt body")
+    ap.add_argument("--column-segments", type=int, default=1, choices=[0, 1, 2],
+                    help="plain 3D steps: 0 z chunks, 1 column segments where the cost model favours them, "
+                         "2 always column segments")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-nz", type=int, default=8, help="physical depth points of the CPU sample")
@@ -400,6 +403,7 @@ def run_ours(args, rank, world, local_rank):
     m0 = (1.0 / w["v0"] ** 2).astype(np.float32)
     mt = (1.0 / w["v_true"] ** 2).astype(np.float32)
     ctx = wave.Context(local_rank)
+    ctx.set_column_segments(args.column_segments)
     stream = torch.cuda.current_stream(dev)
     m0_d = torch.from_numpy(m0).to(dev)
     q_d = torch.from_numpy(q).to(dev)
@@ -511,7 +515,8 @@ def run_ours(args, rank, world, local_rank):
         line = {"metric": METRIC, "value": value, "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": workload_config(w, args.snap if args.mode == "gradient" else None, args.mode),
+                "config": dict(workload_config(w, args.snap if args.mode == "gradient" else None, args.mode),
+                               column_segments={0: "off", 1: "auto", 2: "always"}[args.column_segments]),
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": int(launches), "clocks": clk, "objective": phi}
         print(json.dumps(line), flush=True)
@@ -615,6 +620,7 @@ def run_sweep(args, rank, world, local_rank):
     launches = 0
     clocks = ClockSampler() if rank == 0 else None
     with wave.Context(local_rank) as ctx:
+        ctx.set_column_segments(args.column_segments)
         for so in orders:
             dt = 0.4 * wave.wave_dt_max(w["spacing"], so, w["vmax"])
             q = torch.from_numpy(wave.wave_ricker(args.nt, dt, w["f0"]).reshape(args.nt, 1)).to(dev)

@@ -169,6 +169,22 @@ WAVE_API int wave_context_set_wait_limit_ns(wave_context* ctx, uint64_t ns);
  * levels not 1 or 2). */
 WAVE_API int wave_context_set_time_blocking(wave_context* ctx, int levels);
 
+/* Work decomposition of the plain 3D forward steps (the leapfrog update of
+ * Eq. 1 with the source injection and receiver interpolation of Sec. III-C;
+ * a scheduling choice with no counterpart in the paper).  The default
+ * decomposition cuts each column of 64 x BY points into z chunks of equal
+ * length, one CTA each; on grids that fill the GPU only a few times over, the
+ * last wave of CTAs leaves most of it idle.  Column segments instead lay the
+ * columns end to end and give every resident CTA an equal run of planes
+ * (crossing from one column into the next where it must); such a step also
+ * injects its source row and samples its receiver row itself, so that a time
+ * step is one launch.  mode 1 (the default) takes segments where a cost model
+ * of the two decompositions favours them (grids of fewer than 4 waves), 0
+ * never, 2 always.  Results are identical bit for bit in every mode.  Steps
+ * that store snapshots and the adjoint, gradient and Born sweeps keep the z
+ * chunks.  Errors: INVALID_ARG (ctx NULL, mode not 0, 1 or 2). */
+WAVE_API int wave_context_set_column_segments(wave_context* ctx, int mode);
+
 /* Test hook of the same failure-detection path (no counterpart in the paper):
  * the context's next stencil-step launch issues none of its tile loads, so
  * every wait of its consumer warps runs out after the wait limit, the kernel

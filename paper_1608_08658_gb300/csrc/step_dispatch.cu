@@ -9,7 +9,9 @@ namespace wave {
   int step_smem_r##RR(int ndim, int mode, bool iso);                                                    \
   int step_layout_r##RR(int ndim, int mode, bool iso, int* out);                                        \
   cudaError_t launch_step_batch_r##RR(int ndim, bool iso, const BatchStep* table, int nreq, int ctas, int k,     \
-                                      cudaStream_t s);
+                                      cudaStream_t s);                                                  \
+  cudaError_t launch_step_seg_r##RR(bool iso, const StepMaps& maps, const StepParams& p, const SegWork& w, int ctas, \
+                                    cudaStream_t s);
 WAVE_DECLARE_RADIUS(1)
 WAVE_DECLARE_RADIUS(2)
 WAVE_DECLARE_RADIUS(3)
@@ -45,6 +47,21 @@ cudaError_t launch_step_batch(int R, int ndim, bool iso, const BatchStep* table,
     case 6: return launch_step_batch_r6(ndim, iso, table, nreq, ctas, k, s);
     case 7: return launch_step_batch_r7(ndim, iso, table, nreq, ctas, k, s);
     case 8: return launch_step_batch_r8(ndim, iso, table, nreq, ctas, k, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_step_seg(int R, bool iso, const StepMaps& maps, const StepParams& p, const SegWork& w, int ctas,
+                            cudaStream_t s) {
+  switch (R) {
+    case 1: return launch_step_seg_r1(iso, maps, p, w, ctas, s);
+    case 2: return launch_step_seg_r2(iso, maps, p, w, ctas, s);
+    case 3: return launch_step_seg_r3(iso, maps, p, w, ctas, s);
+    case 4: return launch_step_seg_r4(iso, maps, p, w, ctas, s);
+    case 5: return launch_step_seg_r5(iso, maps, p, w, ctas, s);
+    case 6: return launch_step_seg_r6(iso, maps, p, w, ctas, s);
+    case 7: return launch_step_seg_r7(iso, maps, p, w, ctas, s);
+    case 8: return launch_step_seg_r8(iso, maps, p, w, ctas, s);
     default: return cudaErrorInvalidValue;
   }
 }

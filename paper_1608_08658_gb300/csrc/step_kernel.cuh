@@ -210,13 +210,20 @@ __device__ __forceinline__ void produce(const CUtensorMap& tm_u, const CUtensorM
   }
 }
 
-// Body of one step for the CTA at tile (bx, by) and z chunk bz; the step
-// kernel below runs it once per CTA, the batched step of the serving path
-// (step_batch.cu) for the CTAs of several requests.
-template <int R, int NDIM, int MODE, bool ISO>
+// No extra work for the consumer warps before the first plane.
+struct NoPre {
+  __device__ __forceinline__ void operator()(int) const {}
+};
+
+// Body of one step for the CTA at tile (bx, by), output planes z0 .. z1-1 of
+// its column; the step kernel below runs it once per CTA, the batched step of
+// the serving path for the CTAs of several requests, the segmented step once
+// per column segment of the CTA.  `pre(consumer thread index)` runs on the
+// consumer warps while the producer issues the first loads.
+template <int R, int NDIM, int MODE, bool ISO, class Pre = NoPre>
 __device__ __forceinline__ void step_body(const CUtensorMap& tm_u, const CUtensorMap& tm_p, const CUtensorMap& tm_cm,
                                           const CUtensorMap& tm_g, const CUtensorMap& tm_s, const StepParams& p,
-                                          int bx, int by, int bz) {
+                                          int bx, int by, int z0, int z1, Pre&& pre = Pre{}) {
   using T = StepTraits<R, NDIM, ISO>;
   using L = StepLayout<R, NDIM, MODE, ISO>;
   constexpr int RZ = T::RZ;
@@ -238,8 +245,6 @@ __device__ __forceinline__ void step_body(const CUtensorMap& tm_u, const CUtenso
   const int lane = tid & 31;
   const int x0 = bx * T::BX;
   const int y0 = by * T::BY;
-  const int z0 = bz * p.zchunk;
-  const int z1 = min(z0 + p.zchunk, p.NZ);
   const int nP = z1 - z0;
   const int nU = nP + 2 * RZ;
   if (nP <= 0) return;
@@ -266,6 +271,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap& tm_u, const CUtenso
   }
 
   // ------------------------------------------------------------------ consumers
+  pre(tid);
   const int ty = tid >> 4;  // row of the tile, 0..BY-1
   const int tx = tid & 15;  // quad of 4 x points
   const int gx = x0 + 4 * tx;
@@ -652,7 +658,89 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
     step_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
                 const __grid_constant__ CUtensorMap tm_cm, const __grid_constant__ CUtensorMap tm_g,
                 const __grid_constant__ CUtensorMap tm_s, const StepParams p) {
-  step_body<R, NDIM, MODE, ISO>(tm_u, tm_p, tm_cm, tm_g, tm_s, p, blockIdx.x, blockIdx.y, blockIdx.z);
+  const int z0 = static_cast<int>(blockIdx.z) * p.zchunk;
+  step_body<R, NDIM, MODE, ISO>(tm_u, tm_p, tm_cm, tm_g, tm_s, p, blockIdx.x, blockIdx.y, z0, min(z0 + p.zchunk, p.NZ));
+}
+
+// Receiver sampling of row n from the centre level by the consumer threads of
+// one CTA (share [r0, r1) of the points), with the lane layout and the
+// reduction of gather_kernel: 8 lanes per point, one corner each, summed by
+// xor shuffles.  Whole warps take part in every round.
+template <int NCW>
+__device__ __forceinline__ void sample_share(const GatherSet& gs, const float* __restrict__ field, float* out,
+                                             long long r0, long long r1, int ctid) {
+  const int lane = ctid & 31;
+  const long long lanes = (r1 - r0) * 8;
+  for (long long t0 = static_cast<long long>(ctid - lane); t0 < lanes; t0 += NCW * 32) {
+    const long long t = t0 + lane;
+    const long long pt = r0 + (t >> 3);
+    const int c = static_cast<int>(t & 7);
+    const bool valid = t < lanes;
+    float v = 0.f;
+    if (valid) {
+      const float fx = gs.frac[3 * pt], fy = gs.frac[3 * pt + 1], fz = gs.frac[3 * pt + 2];
+      const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+      float w = (cx ? fx : 1.f - fx) * (cy ? fy : 1.f - fy);
+      w *= (cz ? fz : 1.f - fz);
+      v = __fmul_rn(w, field[gs.base[pt] + cx + cy * gs.sy + cz * gs.sz]);
+    }
+    for (int off = 4; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if (valid && c == 0) out[pt] = v;
+  }
+}
+
+// Segmented plain step (3D, SegWork): CTA b computes planes [b*seg, (b+1)*seg)
+// of the tile-major column sequence, one step body per column it touches (the
+// ring barriers are ended and initialised again in between), samples its share
+// of the receivers from the centre level during its first segment, and then
+// injects source row n into the cells of its segments.
+template <int R, bool ISO>
+__global__ void __launch_bounds__(StepTraits<R, 3, ISO>::NTHREADS, (StepLayout<R, 3, MODE_PLAIN, ISO>::MIN_BLOCKS))
+    step_seg_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
+                    const __grid_constant__ CUtensorMap tm_cm, const __grid_constant__ CUtensorMap tm_g,
+                    const __grid_constant__ CUtensorMap tm_s, const StepParams p, const SegWork w) {
+  using T = StepTraits<R, 3, ISO>;
+  using L = StepLayout<R, 3, MODE_PLAIN, ISO>;
+  const long long g0 = static_cast<long long>(blockIdx.x) * w.seg_planes;
+  const long long g1 = min(g0 + w.seg_planes, w.total);
+  bool first = true;
+  auto pre = [&](int ctid) {
+    if (!first || w.rec_out == nullptr) return;
+    const long long share = (w.rec.n + gridDim.x - 1) / gridDim.x;
+    const long long r0 = min(static_cast<long long>(blockIdx.x) * share, w.rec.n);
+    const long long r1 = min(r0 + share, w.rec.n);
+    sample_share<T::NCW>(w.rec, p.fields + p.cur * p.slot_elems, w.rec_out, r0, r1, ctid);
+  };
+  for (long long g = g0; g < g1;) {
+    const long long col = g / p.NZ;
+    const int z0 = static_cast<int>(g - col * p.NZ);
+    const int z1 = static_cast<int>(min(static_cast<long long>(p.NZ), z0 + (g1 - g)));
+    if (!first) {
+      // every thread is done with the previous segment's ring
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        extern __shared__ unsigned char smem_raw[];
+        uint64_t* bars = reinterpret_cast<uint64_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
+                                                     ~static_cast<uintptr_t>(127));
+        for (int i = 0; i < 2 * (L::NSU + L::NSP); ++i) mbar_inval(&bars[i]);
+      }
+    }
+    step_body<R, 3, MODE_PLAIN, ISO>(tm_u, tm_p, tm_cm, tm_g, tm_s, p, static_cast<int>(col % w.tiles_x),
+                                     static_cast<int>(col / w.tiles_x), z0, z1, pre);
+    first = false;
+    g += z1 - z0;
+  }
+  if (w.inj_vals == nullptr) return;
+  // the new level of the CTA's cells is written; the arithmetic of inject_kernel
+  __syncthreads();
+  float* field = p.fields + p.prev * p.slot_elems;
+  for (int e = w.inj_ptr[blockIdx.x] + static_cast<int>(threadIdx.x); e < w.inj_ptr[blockIdx.x + 1];
+       e += blockDim.x) {
+    const int k = w.inj_list[e];
+    float s = 0.f;
+    for (int i = w.inj.rowptr[k]; i < w.inj.rowptr[k + 1]; ++i) s = fmaf(w.inj.w[i], w.inj_vals[w.inj.pidx[i]], s);
+    field[w.inj.cell[k]] = fmaf(w.inj.coef[k], s, field[w.inj.cell[k]]);
+  }
 }
 
 }  // namespace dev

@@ -52,8 +52,9 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
   const int local = static_cast<int>(blockIdx.x) - e.cta0;
   const int bx = local % e.tiles_x;
   const int by = (local / e.tiles_x) % e.tiles_y;
-  const int bz = local / (e.tiles_x * e.tiles_y);
-  step_body<R, NDIM, MODE_PLAIN, ISO>(e.maps.u, e.maps.p, e.maps.cm, e.maps.g, e.maps.s, *ps, bx, by, bz);
+  const int z0 = local / (e.tiles_x * e.tiles_y) * ps->zchunk;
+  step_body<R, NDIM, MODE_PLAIN, ISO>(e.maps.u, e.maps.p, e.maps.cm, e.maps.g, e.maps.s, *ps, bx, by, z0,
+                                      min(z0 + ps->zchunk, ps->NZ));
 }
 
 }  // namespace dev
@@ -84,6 +85,34 @@ static cudaError_t launch_batch_one(bool iso, const BatchStep* table, int nreq, 
     if (iso) return launch_batch_iso<R, NDIM, true>(table, nreq, ctas, k, s);
   }
   return launch_batch_iso<R, NDIM, false>(table, nreq, ctas, k, s);
+}
+
+template <int R, bool ISO>
+static cudaError_t launch_seg_iso(const StepMaps& maps, const StepParams& p, const SegWork& w, int ctas,
+                                  cudaStream_t stream) {
+  using T = StepTraits<R, 3, ISO>;
+  using L = StepLayout<R, 3, MODE_PLAIN, ISO>;
+  static std::atomic<unsigned long long> configured{0};
+  int device = 0;
+  cudaError_t e = cudaGetDevice(&device);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (device & 63);
+  if (!(configured.load(std::memory_order_acquire) & bit)) {
+    e = cudaFuncSetAttribute(dev::step_seg_kernel<R, ISO>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM);
+    if (e != cudaSuccess) return e;
+    configured.fetch_or(bit, std::memory_order_acq_rel);
+  }
+  dev::step_seg_kernel<R, ISO><<<ctas, T::NTHREADS, L::SMEM, stream>>>(maps.u, maps.p, maps.cm, maps.g, maps.s, p, w);
+  return cudaGetLastError();
+}
+
+template <int R>
+static cudaError_t launch_seg_one(bool iso, const StepMaps& maps, const StepParams& p, const SegWork& w, int ctas,
+                                  cudaStream_t s) {
+  if constexpr (R >= kIsoMinR) {
+    if (iso) return launch_seg_iso<R, true>(maps, p, w, ctas, s);
+  }
+  return launch_seg_iso<R, false>(maps, p, w, ctas, s);
 }
 
 // Host launcher for one radius; instantiated once per step_r<R>.cu.
@@ -196,6 +225,10 @@ static int layout_modes(int mode, int* out) {
                                       cudaStream_t s) {                                                 \
     return ndim == 3 ? launch_batch_one<RR, 3>(iso, table, nreq, ctas, k, s)                            \
                      : launch_batch_one<RR, 2>(iso, table, nreq, ctas, k, s);                           \
+  }                                                                                                     \
+  cudaError_t launch_step_seg_r##RR(bool iso, const StepMaps& maps, const StepParams& p, const SegWork& w, int ctas, \
+                                    cudaStream_t s) {                                                   \
+    return launch_seg_one<RR>(iso, maps, p, w, ctas, s);                                                \
   }                                                                                                     \
   int step_layout_r##RR(int ndim, int mode, bool iso, int* out) {                                       \
     if (iso_kernel(RR, iso))                                                                            \

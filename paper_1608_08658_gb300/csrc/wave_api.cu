@@ -42,6 +42,12 @@ struct PointSetDev {
   int* pidx = nullptr;
   float* w = nullptr;
   float* coef = nullptr;
+  std::vector<long long> cells_host;  // the cells, for the segment lists below
+  // cells per CTA of the segmented step (CSR), for the decomposition seg_key
+  uint64_t seg_key = 0;
+  std::vector<int> seg_ptr_h, seg_list_h;
+  int* seg_ptr = nullptr;
+  int* seg_list = nullptr;
 };
 
 struct Pending {
@@ -76,6 +82,7 @@ struct wave_context {
   unsigned long long wait_ns = kWaitLimitNs;  // limit of the step kernels' progress waits
   int sm_count = 152;                         // multiprocessors of the device
   int time_block = 1;                         // time levels per pass of source-free forward modelling
+  int col_segments = 1;                       // segmented plain step: 0 never, 1 where faster, 2 always (3D)
   bool withhold_next = false;                 // test hook: the next step launch issues no loads
   int last_plan[4] = {0, 0, 0, 0};  // fmt, buffer levels, parts per segment, segments
   // side stream and events that copy finished receiver rows to a pinned host
@@ -379,6 +386,9 @@ struct Prob {
   float em[3] = {0, 0, 0};       // eta_max/nbl^2 per kernel axis
   StepParams sp{};
   dim3 grid;
+  // segmented plain step (3D): CTAs and planes per CTA (0: z chunks only)
+  int seg_ctas = 0, seg_planes = 0;
+  int tiles_x = 0, tiles_y = 0;
 };
 
 // Number of chunks the streamed axis (NZ planes) is cut into; the grid has
@@ -407,6 +417,30 @@ int choose_chunks(long long tiles, int NZ, int R, long long slots) {
   for (int c = lo; c <= hi; ++c)
     if (fill(c) >= best_fill - 0.01) return c;
   return lo;
+}
+
+// Planes per CTA of the segmented plain step, or 0 to keep the z chunks.  The
+// z-chunk grid of `chunks` per column runs in ceil(tiles c / slots) waves of
+// NZ/c planes; one wave of equal column runs takes W = tiles NZ / slots planes
+// per CTA.  Each column segment costs about R/2 + 1 plane times to fill its
+// register queue (the 2R planes of its z halo, loaded with a few in flight),
+// and the slowest run has floor((W-1)/NZ) + 2 segments.  Segments are taken
+// for grids of fewer than 4 waves where that estimate is at least 3 % shorter
+// (or always, with `force`), with runs of at least max(16, 2R) planes.  Larger
+// grids keep the z chunks, whose concurrent CTAs share their halo planes in L2.
+int seg_planes_for(long long tiles, int NZ, int chunks, int R, long long slots, bool force) {
+  const long long total = tiles * NZ;
+  const long long min_run = std::max(16, 2 * R);
+  long long ctas = std::min(slots, std::max<long long>(1, total / min_run));
+  const long long W = (total + ctas - 1) / ctas;
+  if (W > (1LL << 30)) return 0;
+  if (force) return static_cast<int>(W);
+  const double fill = R / 2.0 + 1.0;
+  const double waves = std::ceil(double(tiles * chunks) / double(slots));
+  if (waves >= 4) return 0;
+  const double t_chunks = waves * (double(NZ) / chunks + fill);
+  const double t_seg = double(W) + double((W - 1) / NZ + 2) * fill;
+  return t_seg < 0.97 * t_chunks ? static_cast<int>(W) : 0;
 }
 
 int prepare(wave_context* ctx, const wave_geometry* geom, float dt, int nt, int so, Prob* P) {
@@ -513,6 +547,19 @@ int prepare(wave_context* ctx, const wave_geometry* geom, float dt, int nt, int 
   chunks = (g.NZ + sp.zchunk - 1) / sp.zchunk;
   if (ty > 65535 || chunks > 65535) return fail(ctx, WAVE_ERR_NOT_SUPPORTED, "grid too large for one launch");
   P->grid = dim3(tx, ty, chunks);
+  P->tiles_x = tx;
+  P->tiles_y = ty;
+  if (nd == 3 && ctx && ctx->col_segments != 0) {
+    int layout[kStepLayoutMax];
+    const int per_sm = step_layout(P->R, nd, MODE_PLAIN, sp.iso != 0, layout) > 8 ? layout[8] : 2;
+    const long long slots = static_cast<long long>(ctx->sm_count) * per_sm;
+    const int W = seg_planes_for(static_cast<long long>(tx) * ty, g.NZ, chunks, P->R, slots, ctx->col_segments == 2);
+    if (W > 0) {
+      const long long total = static_cast<long long>(tx) * ty * g.NZ;
+      P->seg_planes = W;
+      P->seg_ctas = static_cast<int>((total + W - 1) / W);
+    }
+  }
   return WAVE_OK;
 }
 
@@ -762,6 +809,8 @@ int upload_points(wave_context* ctx, const PointsHost& H, PointSetDev& e, cudaSt
   e.n = H.n;
   e.ncell = static_cast<int>(H.cells.size());
   e.key = H.key;
+  e.cells_host = H.cells;
+  e.seg_key = 0;
   e.valid = true;
   return WAVE_OK;
 }
@@ -879,11 +928,90 @@ int alloc_snapshots(wave_context* ctx, Prob& P, int fmt, int levels, SnapStore* 
   return snapshot_map(ctx, P, fmt, S->data, levels, &S->map);
 }
 
+// Cells of an injection set per CTA of the segmented step (CSR over the
+// CTAs, device copies in the workspace), kept on the point set for the
+// decomposition they were made for.
+int seg_cell_lists(wave_context* ctx, const Prob& P, PointSetDev* ps, cudaStream_t s) {
+  const int bx = step_bx(), by = step_by(P.R, P.ndim, P.sp.iso != 0);
+  uint64_t key = 1469598103934665603ull;
+  const long long dims[7] = {P.seg_planes, P.seg_ctas, P.tiles_x, P.g.NZ, P.g.NY, P.g.pitch, by};
+  key = fnv(key, dims, sizeof(dims));
+  if (ps->seg_key == key && ps->seg_ptr) return WAVE_OK;
+  const int ctas = P.seg_ctas;
+  std::vector<int> owner(ps->cells_host.size());
+  ps->seg_ptr_h.assign(static_cast<size_t>(ctas) + 1, 0);
+  for (size_t k = 0; k < owner.size(); ++k) {
+    const long long c = ps->cells_host[k];
+    const int x = static_cast<int>(c % P.g.pitch);
+    const long long r = c / P.g.pitch;
+    const int y = static_cast<int>(r % P.g.NY);
+    const int z = static_cast<int>(r / P.g.NY);
+    const long long col = static_cast<long long>(y / by) * P.tiles_x + x / bx;
+    owner[k] = static_cast<int>((col * P.g.NZ + z) / P.seg_planes);
+    ps->seg_ptr_h[owner[k] + 1]++;
+  }
+  for (int b = 0; b < ctas; ++b) ps->seg_ptr_h[b + 1] += ps->seg_ptr_h[b];
+  ps->seg_list_h.assign(std::max<size_t>(1, owner.size()), 0);
+  std::vector<int> fill(ps->seg_ptr_h.begin(), ps->seg_ptr_h.end() - 1);
+  for (size_t k = 0; k < owner.size(); ++k) ps->seg_list_h[fill[owner[k]]++] = static_cast<int>(k);
+  void* p = nullptr;
+  TRY(ws_get(ctx, ps->tag + "segptr", ps->seg_ptr_h.size() * 4, &p));
+  ps->seg_ptr = static_cast<int*>(p);
+  TRY(ws_get(ctx, ps->tag + "seglist", ps->seg_list_h.size() * 4, &p));
+  ps->seg_list = static_cast<int*>(p);
+  // the host vectors stay with the point set until the copies are done
+  CK(cudaMemcpyAsync(ps->seg_ptr, ps->seg_ptr_h.data(), ps->seg_ptr_h.size() * 4, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ps->seg_list, ps->seg_list_h.data(), ps->seg_list_h.size() * 4, cudaMemcpyHostToDevice, s));
+  ps->seg_key = key;
+  return WAVE_OK;
+}
+
+// Plain forward steps n = n0 .. n1-1 by the segmented step: step n injects
+// row n of q into level n+1 and samples receiver row n from level n (n > n0);
+// row n1 is sampled after the last step.
+int forward_steps_seg(wave_context* ctx, Prob& P, Work& W, int n0, int n1, const float* q, PointSetDev* src,
+                      float* d, PointSetDev* rec, cudaStream_t s) {
+  SegWork w{};
+  w.seg_planes = P.seg_planes;
+  w.tiles_x = P.tiles_x;
+  w.tiles_y = P.tiles_y;
+  w.total = static_cast<long long>(P.tiles_x) * P.tiles_y * P.g.NZ;
+  w.inj = inject_set(src);
+  if (w.inj.n > 0) {
+    TRY(seg_cell_lists(ctx, P, src, s));
+    w.inj_ptr = src->seg_ptr;
+    w.inj_list = src->seg_list;
+  }
+  const bool sample = rec && rec->n > 0 && d;
+  if (sample) w.rec = gather_set(P, rec);
+  for (int n = n0; n < n1; ++n) {
+    P.sp.cur = fslot(n);
+    P.sp.prev = fslot(n - 1);
+    StepParams sp = P.sp;
+    if (ctx->withhold_next) {
+      sp.withhold = 1;
+      ctx->withhold_next = false;
+    }
+    w.inj_vals = w.inj.n > 0 ? q + static_cast<long long>(n) * src->n : nullptr;
+    w.rec_out = sample && n > n0 ? d + static_cast<long long>(n) * rec->n : nullptr;
+    TRY(launch(ctx, WAVE_KERNEL_STEP, s,
+               [&] { return launch_step_seg(P.R, sp.iso != 0, W.maps, sp, w, P.seg_ctas, s); }));
+  }
+  if (sample && n1 > n0) {
+    GatherSet grec = gather_set(P, rec);
+    float* row = d + static_cast<long long>(n1) * rec->n;
+    const float* level = slot_ptr(W, P, fslot(n1));
+    TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_gather(grec, level, row, s); }));
+  }
+  return WAVE_OK;
+}
+
 // Forward steps n = n0 .. n1-1 (each produces u^{n+1}); q rows injected; receiver
 // rows gathered when d is given; centre levels n >= snap_from stored at
 // level n - snap_base when S is given.
 int forward_steps(wave_context* ctx, Prob& P, Work& W, int n0, int n1, const float* q, PointSetDev* src,
                   float* d, PointSetDev* rec, SnapStore* S, int snap_from, int snap_base, cudaStream_t s) {
+  if (P.seg_ctas > 0 && (!S || n1 <= snap_from)) return forward_steps_seg(ctx, P, W, n0, n1, q, src, d, rec, s);
   InjectSet isrc = inject_set(src);
   GatherSet grec = rec ? gather_set(P, rec) : GatherSet{};
   for (int n = n0; n < n1; ++n) {
@@ -1754,6 +1882,13 @@ int wave_context_set_wait_limit_ns(wave_context* ctx, uint64_t ns) {
 int wave_context_set_time_blocking(wave_context* ctx, int levels) {
   if (!ctx || (levels != 1 && levels != 2)) return WAVE_ERR_INVALID_ARG;
   ctx->time_block = levels;
+  return WAVE_OK;
+}
+
+int wave_context_set_column_segments(wave_context* ctx, int mode) {
+  if (!ctx) return WAVE_ERR_INVALID_ARG;
+  if (mode < 0 || mode > 2) return fail(ctx, WAVE_ERR_INVALID_ARG, "column segment mode must be 0, 1 or 2");
+  ctx->col_segments = mode;
   return WAVE_OK;
 }
 

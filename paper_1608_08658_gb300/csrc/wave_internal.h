@@ -324,6 +324,29 @@ struct BatchSparse {
   int gcta0;               // first CTA of the request's gather in the launch
 };
 
+// Column segments of the plain 3D step, for grids of few CTA waves: the
+// tiles_x * tiles_y columns of NZ planes, tile after tile, form one sequence
+// of `total` planes, cut into runs of seg_planes, one run per CTA (a run may
+// end in one column and go on at the top of the next).  Such a launch also
+// does the step's sparse work: the injection of source row n into the cells
+// of the CTA's runs once its planes are written (inj_vals = row n, or null),
+// and the sampling of receiver row n from the centre level, a share of the
+// receivers per CTA, while its first planes load (rec_out = row n, or null).
+struct SegWork {
+  int seg_planes;
+  int tiles_x, tiles_y;
+  long long total;
+  InjectSet inj;
+  const int* inj_ptr;      // [ctas + 1]: the CTA's cells in inj_list
+  const int* inj_list;     // indices into inj, grouped by CTA
+  const float* inj_vals;   // source row n, or null
+  GatherSet rec;
+  float* rec_out;          // receiver row n, or null
+};
+// Segmented plain step (3D) of `ctas` CTAs; the variant of p.iso.
+cudaError_t launch_step_seg(int R, bool iso, const StepMaps& maps, const StepParams& p, const SegWork& w, int ctas,
+                            cudaStream_t stream);
+
 cudaError_t launch_gather(const GatherSet& gs, const float* field, float* out_row, cudaStream_t s);
 cudaError_t launch_inject_coef(const InjectSet& is, const GridDims& g, const float* cm,
                                const float* eta_max_over_nbl2, float half_inv_dt, cudaStream_t s);

@@ -69,6 +69,7 @@ _SIGS = {
     "wave_context_set_wait_limit_ns": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "wave_context_withhold_next_loads": (ctypes.c_int, [_P]),
     "wave_context_set_time_blocking": (ctypes.c_int, [_P, ctypes.c_int]),
+    "wave_context_set_column_segments": (ctypes.c_int, [_P, ctypes.c_int]),
     "wave_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "wave_last_error": (ctypes.c_char_p, [_P]),
     "wave_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, ctypes.c_int, _P]),
@@ -288,6 +289,10 @@ class Context:
     def set_time_blocking(self, levels):
         """Time levels per pass of source-free forward modelling (1 or 2)."""
         _check(self, lib().wave_context_set_time_blocking(self.handle, int(levels)))
+
+    def set_column_segments(self, mode):
+        """Decomposition of plain 3D forward steps: 0 z chunks, 1 automatic, 2 column segments."""
+        _check(self, lib().wave_context_set_column_segments(self.handle, int(mode)))
 
     def withhold_next_loads(self):
         """Test hook: the next step launch issues no tile loads (its waits run out)."""
