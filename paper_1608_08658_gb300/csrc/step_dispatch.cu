@@ -97,7 +97,13 @@ int step_layout(int R, int ndim, int mode, bool iso, int* out) {
 int step_bx() { return StepTraits<1, 3>::BX; }
 int step_by(int R, int ndim, bool iso) {
   if (ndim != 3) return StepTraits<1, 2>::BY;
-  if (iso_kernel(R, iso)) return R == 7 ? StepTraits<7, 3, true>::BY : StepTraits<8, 3, true>::BY;
+  if (iso_kernel(R, iso)) {
+    switch (R) {
+      case 6: return StepTraits<6, 3, true>::BY;
+      case 7: return StepTraits<7, 3, true>::BY;
+      default: return StepTraits<8, 3, true>::BY;
+    }
+  }
   switch (R) {
     case 1: return StepTraits<1, 3>::BY;
     case 2: return StepTraits<2, 3>::BY;

@@ -665,27 +665,43 @@ __global__ void __launch_bounds__(StepTraits<R, NDIM, ISO>::NTHREADS, (StepLayou
 // Receiver sampling of row n from the centre level by the consumer threads of
 // one CTA (share [r0, r1) of the points), with the lane layout and the
 // reduction of gather_kernel: 8 lanes per point, one corner each, summed by
-// xor shuffles.  Whole warps take part in every round.
-template <int NCW>
+// xor shuffles.  Whole warps take part in every round; the loads of KR rounds
+// are issued before any of their values is used, so that a CTA's share costs
+// a few memory latencies, hidden behind the loads of its first planes.
+template <int NCW, int KR>
 __device__ __forceinline__ void sample_share(const GatherSet& gs, const float* __restrict__ field, float* out,
                                              long long r0, long long r1, int ctid) {
+  constexpr int STRIDE = NCW * 32;
   const int lane = ctid & 31;
+  const int c = lane & 7;
+  const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
   const long long lanes = (r1 - r0) * 8;
-  for (long long t0 = static_cast<long long>(ctid - lane); t0 < lanes; t0 += NCW * 32) {
-    const long long t = t0 + lane;
-    const long long pt = r0 + (t >> 3);
-    const int c = static_cast<int>(t & 7);
-    const bool valid = t < lanes;
-    float v = 0.f;
-    if (valid) {
-      const float fx = gs.frac[3 * pt], fy = gs.frac[3 * pt + 1], fz = gs.frac[3 * pt + 2];
-      const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
-      float w = (cx ? fx : 1.f - fx) * (cy ? fy : 1.f - fy);
-      w *= (cz ? fz : 1.f - fz);
-      v = __fmul_rn(w, field[gs.base[pt] + cx + cy * gs.sy + cz * gs.sz]);
+  for (long long t0 = static_cast<long long>(ctid - lane); t0 < lanes; t0 += KR * STRIDE) {
+    float w[KR], v[KR];
+    long long at[KR];
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      const long long t = t0 + k * STRIDE + lane;
+      w[k] = 0.f;
+      at[k] = -1;
+      if (t < lanes) {
+        const long long pt = r0 + (t >> 3);
+        const float fx = gs.frac[3 * pt], fy = gs.frac[3 * pt + 1], fz = gs.frac[3 * pt + 2];
+        float wk = (cx ? fx : 1.f - fx) * (cy ? fy : 1.f - fy);
+        wk *= (cz ? fz : 1.f - fz);
+        w[k] = wk;
+        at[k] = gs.base[pt] + cx + cy * gs.sy + cz * gs.sz;
+      }
     }
-    for (int off = 4; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (valid && c == 0) out[pt] = v;
+#pragma unroll
+    for (int k = 0; k < KR; ++k) v[k] = at[k] >= 0 ? __fmul_rn(w[k], field[at[k]]) : 0.f;
+#pragma unroll
+    for (int k = 0; k < KR; ++k) {
+      float x = v[k];
+      for (int off = 4; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+      const long long t = t0 + k * STRIDE + lane;
+      if (t < lanes && c == 0) out[r0 + (t >> 3)] = x;
+    }
   }
 }
 
@@ -709,7 +725,7 @@ __global__ void __launch_bounds__(StepTraits<R, 3, ISO>::NTHREADS, (StepLayout<R
     const long long share = (w.rec.n + gridDim.x - 1) / gridDim.x;
     const long long r0 = min(static_cast<long long>(blockIdx.x) * share, w.rec.n);
     const long long r1 = min(r0 + share, w.rec.n);
-    sample_share<T::NCW>(w.rec, p.fields + p.cur * p.slot_elems, w.rec_out, r0, r1, ctid);
+    sample_share<T::NCW, (T::NCW == 8 && R >= 5) ? 4 : 8>(w.rec, p.fields + p.cur * p.slot_elems, w.rec_out, r0, r1, ctid);
   };
   for (long long g = g0; g < g1;) {
     const long long col = g / p.NZ;

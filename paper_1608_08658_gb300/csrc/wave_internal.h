@@ -58,9 +58,9 @@ constexpr int kSlabY = 2;
 // Radius from which the lead-plane design is used (every mode).
 constexpr int kLeadMinR = 7;
 // Radius from which equal spacing on every axis selects the kernel variant
-// with one coefficient per offset (measured faster from radius 7 on, slower at
-// radius 5-6, equal below).
-constexpr int kIsoMinR = 7;
+// with one coefficient per offset (with 14-row tiles at 128 registers: order 12
+// forward step 0.645 -> 0.579 ms on 592^3; order 14 and 16 likewise faster).
+constexpr int kIsoMinR = 6;
 __host__ __device__ constexpr bool iso_kernel(int R, bool equal_spacing) { return equal_spacing && R >= kIsoMinR; }
 // Planes per renamed register-queue group where a full period of 2R+1 planes
 // would spill (see StepLayout::UR).
@@ -75,10 +75,11 @@ template <int R, int NDIM, bool ISO = false>
 struct StepTraits {
   static constexpr int BX = 64;                   // x outputs per CTA (16 threads x 4)
   // axis-1 outputs per CTA (one row per 16 threads, two rows per warp); 3D
-  // radius 8, and radius 7 with the equal-spacing kernel, use 14 rows so that
-  // a CTA has 8 warps and two CTAs fit the register file at 128 registers per
-  // thread (measured slower for the general radius-7 kernel)
-  static constexpr int BY = (NDIM == 3 && (R >= 8 || (R == 7 && ISO))) ? 14 : 16;
+  // radius 8, and radius 6-7 with the equal-spacing kernel, use 14 rows so
+  // that a CTA has 8 warps and two CTAs fit the register file at 128 registers
+  // per thread (measured slower for the general radius-7 kernel; the order-12
+  // equal-spacing step 0.594 -> 0.579 ms against 16 rows at 96 registers)
+  static constexpr int BY = (NDIM == 3 && (R >= 8 || (R >= 6 && ISO))) ? 14 : 16;
   static constexpr int HX = (R <= 4) ? 4 : 8;     // x halo, rounded to 16 bytes for TMA
   static constexpr int RZ = (NDIM == 3) ? R : 0;  // halo along the streamed axis
   static constexpr int UW = BX + 2 * HX;          // smem row length of a halo box (floats)

@@ -93,7 +93,7 @@ def test_step_kernel_layout(lib):
                 for eq in (0, 1):
                     L = wave.wave_step_kernel_layout(so, ndim, kernel, eq)
                     assert (L["radius"], L["ndim"], L["kernel"]) == (R, ndim, kernel)
-                    assert L["equal_spacing_variant"] == int(bool(eq) and R >= 7)
+                    assert L["equal_spacing_variant"] == int(bool(eq) and R >= 6)
                     assert L["bx"] % 4 == 0 and L["hx"] % 4 == 0 and L["hx"] >= min(R, 8) - 4
                     assert L["threads"] == (L["by"] // 2 + 1) * 32
                     assert L["smem_bytes"] <= smem_two_ctas
