@@ -185,6 +185,24 @@ WAVE_API int wave_context_set_time_blocking(wave_context* ctx, int levels);
  * chunks.  Errors: INVALID_ARG (ctx NULL, mode not 0, 1 or 2). */
 WAVE_API int wave_context_set_column_segments(wave_context* ctx, int mode);
 
+/* Host-only: the column segments the plain 3D step takes for a grid of
+ * `columns` columns (x tiles of 64 times axis-1 tiles of BY points) of nz
+ * planes, whose z-chunk grid has `chunks` chunks per column, with `slots`
+ * resident CTAs.  A CTA's cost is its planes plus 4 + R plane times for every
+ * column segment it starts (the fill of its register queue); the runs are cut
+ * along the tile-major plane sequence so that the largest cost is as small as
+ * the run count allows, at most one run per max(16, 2R) planes and per slot.
+ * Segments are taken for grids of fewer than 4 waves where that cost is at
+ * least 3 % below the z-chunk grid's, or always with force != 0.
+ *   run_start: out, n_runs + 1 entries: run b covers planes
+ *              [run_start[b], run_start[b+1]) of the sequence (column c holds
+ *              planes c*nz .. c*nz + nz - 1); may be NULL when cap = 0;
+ *   n_runs:    out, the number of runs, 0 where the z chunks are kept.
+ * Errors: INVALID_ARG (columns, nz, chunks or slots < 1, space_order not even
+ * in [2, 16], n_runs NULL, more than cap - 1 runs). */
+WAVE_API int wave_column_runs_for(long long columns, int nz, int chunks, int space_order, long long slots, int force,
+                                  long long* run_start, int cap, int* n_runs);
+
 /* Test hook of the same failure-detection path (no counterpart in the paper):
  * the context's next stencil-step launch issues none of its tile loads, so
  * every wait of its consumer warps runs out after the wait limit, the kernel

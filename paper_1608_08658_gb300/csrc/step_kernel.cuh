@@ -483,7 +483,6 @@ __device__ __forceinline__ void step_body(const CUtensorMap& tm_u, const CUtenso
       lb = __fadd2_rn(lb, make_float2(src.z, src.w));
     }
 
-    const float4 lap = make_float4(la.x, la.y, lb.x, lb.y);
     const int gz = z0 + j;
     const float ez = NDIM == 3 ? sponge_term(gz, p.NZ, p.nblz, p.emz) : 0.f;
     float4 out;
@@ -497,16 +496,36 @@ __device__ __forceinline__ void step_body(const CUtensorMap& tm_u, const CUtenso
       const float2 ob = __ffma2_rn(make_float2(cm.z, cm.w), lb,
                                    __ffma2_rn(m1, make_float2(prev.z, prev.w), __fadd2_rn(cb, cb)));
       out = make_float4(oa.x, oa.y, ob.x, ob.y);
+    } else if constexpr (L::PACKED_DAMP) {
+      // damped, on packed pairs: the operations of damp_inv and of the update
+      // below, each rounded once, so the same values as one point at a time
+      const float2 hv = make_float2(p.half_inv_dt, p.half_inv_dt);
+      const float2 one = make_float2(1.f, 1.f);
+      auto damped = [&](float ea, float eb, float2 cmv, float2 lv, float2 pv, float2 cv) -> float2 {
+        const float2 eta = make_float2(sponge_sum(ea, ez), sponge_sum(eb, ez));
+        const float2 k = __fmul2_rn(__fmul2_rn(eta, cmv), hv);
+        const float2 omk = __fadd2_rn(one, make_float2(-k.x, -k.y));
+        const float2 d = __fadd2_rn(one, k);
+        const float2 inv =
+            make_float2(eta.x == 0.f ? 1.f : __fdividef(1.f, d.x), eta.y == 0.f ? 1.f : __fdividef(1.f, d.y));
+        const float2 t = __ffma2_rn(make_float2(-omk.x, -omk.y), pv, __fadd2_rn(cv, cv));
+        return __fmul2_rn(__ffma2_rn(cmv, lv, t), inv);
+      };
+      const float2 oa = damped(exy[0], exy[1], make_float2(cm.x, cm.y), la, make_float2(prev.x, prev.y),
+                               make_float2(c.x, c.y));
+      const float2 ob = damped(exy[2], exy[3], make_float2(cm.z, cm.w), lb, make_float2(prev.z, prev.w),
+                               make_float2(c.z, c.w));
+      out = make_float4(oa.x, oa.y, ob.x, ob.y);
     } else {
       float omk;
       float inv = damp_inv(sponge_sum(exy[0], ez), cm.x, p.half_inv_dt, omk);
-      out.x = fmaf(cm.x, lap.x, fmaf(-omk, prev.x, 2.f * c.x)) * inv;
+      out.x = fmaf(cm.x, la.x, fmaf(-omk, prev.x, 2.f * c.x)) * inv;
       inv = damp_inv(sponge_sum(exy[1], ez), cm.y, p.half_inv_dt, omk);
-      out.y = fmaf(cm.y, lap.y, fmaf(-omk, prev.y, 2.f * c.y)) * inv;
+      out.y = fmaf(cm.y, la.y, fmaf(-omk, prev.y, 2.f * c.y)) * inv;
       inv = damp_inv(sponge_sum(exy[2], ez), cm.z, p.half_inv_dt, omk);
-      out.z = fmaf(cm.z, lap.z, fmaf(-omk, prev.z, 2.f * c.z)) * inv;
+      out.z = fmaf(cm.z, lb.x, fmaf(-omk, prev.z, 2.f * c.z)) * inv;
       inv = damp_inv(sponge_sum(exy[3], ez), cm.w, p.half_inv_dt, omk);
-      out.w = fmaf(cm.w, lap.w, fmaf(-omk, prev.w, 2.f * c.w)) * inv;
+      out.w = fmaf(cm.w, lb.y, fmaf(-omk, prev.w, 2.f * c.w)) * inv;
     }
     if (store_ok) *reinterpret_cast<float4*>(out_base + idx) = out;
 
@@ -705,8 +724,8 @@ __device__ __forceinline__ void sample_share(const GatherSet& gs, const float* _
   }
 }
 
-// Segmented plain step (3D, SegWork): CTA b computes planes [b*seg, (b+1)*seg)
-// of the tile-major column sequence, one step body per column it touches (the
+// Segmented plain step (3D, SegWork): CTA b computes its run of the tile-major
+// column sequence, one step body per column it touches (the
 // ring barriers are ended and initialised again in between), samples its share
 // of the receivers from the centre level during its first segment, and then
 // injects source row n into the cells of its segments.
@@ -717,8 +736,8 @@ __global__ void __launch_bounds__(StepTraits<R, 3, ISO>::NTHREADS, (StepLayout<R
                     const __grid_constant__ CUtensorMap tm_s, const StepParams p, const SegWork w) {
   using T = StepTraits<R, 3, ISO>;
   using L = StepLayout<R, 3, MODE_PLAIN, ISO>;
-  const long long g0 = static_cast<long long>(blockIdx.x) * w.seg_planes;
-  const long long g1 = min(g0 + w.seg_planes, w.total);
+  const long long g0 = w.run_start[blockIdx.x];
+  const long long g1 = w.run_start[blockIdx.x + 1];
   bool first = true;
   auto pre = [&](int ctid) {
     if (!first || w.rec_out == nullptr) return;

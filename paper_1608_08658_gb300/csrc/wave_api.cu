@@ -386,8 +386,10 @@ struct Prob {
   float em[3] = {0, 0, 0};       // eta_max/nbl^2 per kernel axis
   StepParams sp{};
   dim3 grid;
-  // segmented plain step (3D): CTAs and planes per CTA (0: z chunks only)
-  int seg_ctas = 0, seg_planes = 0;
+  // segmented plain step (3D): CTAs (0: z chunks only) and the start of each
+  // CTA's run in the tile-major plane sequence (seg_ctas + 1 entries)
+  int seg_ctas = 0;
+  std::vector<long long> seg_runs;
   int tiles_x = 0, tiles_y = 0;
 };
 
@@ -419,28 +421,73 @@ int choose_chunks(long long tiles, int NZ, int R, long long slots) {
   return lo;
 }
 
-// Planes per CTA of the segmented plain step, or 0 to keep the z chunks.  The
-// z-chunk grid of `chunks` per column runs in ceil(tiles c / slots) waves of
-// NZ/c planes; one wave of equal column runs takes W = tiles NZ / slots planes
-// per CTA.  Each column segment costs about R/2 + 1 plane times to fill its
-// register queue (the 2R planes of its z halo, loaded with a few in flight),
-// and the slowest run has floor((W-1)/NZ) + 2 segments.  Segments are taken
-// for grids of fewer than 4 waves where that estimate is at least 3 % shorter
-// (or always, with `force`), with runs of at least max(16, 2R) planes.  Larger
-// grids keep the z chunks, whose concurrent CTAs share their halo planes in L2.
-int seg_planes_for(long long tiles, int NZ, int chunks, int R, long long slots, bool force) {
+// Column runs of the segmented plain step.  A CTA's cost is its planes plus
+// kSegFill(R) plane times for each column segment it starts (the fill of its
+// register queue: the 2R planes of the z halo, loaded a few at a time).  For a
+// cost bound C the runs are cut greedily along the tile-major plane sequence
+// (a run that reaches a column's end goes on in the next column if its budget
+// allows, paying another fill); the smallest C that needs no more than `ctas`
+// runs is found by bisection, so that runs crossing a column are shorter by
+// about one fill.  Returns the run starts (runs + 1 entries) and C.
+double seg_fill(int R) { return 4.0 + R; }
+
+double seg_cut(long long tiles, int NZ, double fill, double C, std::vector<long long>* runs) {
+  const long long total = tiles * NZ;
+  long long g = 0, n = 0;
+  double worst = 0;
+  if (runs) runs->assign(1, 0);
+  while (g < total) {
+    double budget = C - fill;
+    double cost = fill;
+    long long end = g;
+    while (true) {
+      const long long e = NZ - end % NZ;  // planes left in this column
+      if (budget < e) {
+        const long long take = std::max<long long>(end == g ? 1 : 0, static_cast<long long>(budget));
+        end += take;
+        cost += static_cast<double>(take);
+        break;
+      }
+      end += e;
+      cost += static_cast<double>(e);
+      budget -= static_cast<double>(e) + fill;
+      if (end >= total || budget < 1.0) break;
+      cost += fill;
+    }
+    end = std::min(end, total);
+    worst = std::max(worst, cost);
+    g = end;
+    ++n;
+    if (runs) runs->push_back(g);
+  }
+  return runs ? worst : static_cast<double>(n);
+}
+
+// Plans the segmented step for a grid of `tiles` columns of NZ planes whose
+// z-chunk grid has `chunks` chunks per column and `slots` resident CTAs; true
+// (and the run starts) where segments are taken.  The z-chunk grid runs in
+// ceil(tiles c / slots) waves of NZ/c planes plus a fill; the runs cost the
+// bound found above.  Segments are taken for grids of fewer than 4 waves where
+// that is at least 3 % shorter (or always, with `force`), with at most one run
+// per max(16, 2R) planes.  Larger grids keep the z chunks, whose concurrent
+// CTAs share their halo planes in L2.
+bool seg_plan(long long tiles, int NZ, int chunks, int R, long long slots, bool force, std::vector<long long>* runs) {
   const long long total = tiles * NZ;
   const long long min_run = std::max(16, 2 * R);
-  long long ctas = std::min(slots, std::max<long long>(1, total / min_run));
-  const long long W = (total + ctas - 1) / ctas;
-  if (W > (1LL << 30)) return 0;
-  if (force) return static_cast<int>(W);
-  const double fill = R / 2.0 + 1.0;
+  const long long ctas = std::min(slots, std::max<long long>(1, total / min_run));
+  const double fill = seg_fill(R);
   const double waves = std::ceil(double(tiles * chunks) / double(slots));
-  if (waves >= 4) return 0;
+  if (!force && waves >= 4) return false;
+  double lo = double(total) / double(ctas), hi = lo + 2.0 * fill + 1.0;
+  while (seg_cut(tiles, NZ, fill, hi, nullptr) > double(ctas)) hi += fill;
+  for (int it = 0; it < 50 && hi - lo > 0.25; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (seg_cut(tiles, NZ, fill, mid, nullptr) <= double(ctas)) hi = mid;
+    else lo = mid;
+  }
+  const double t_seg = seg_cut(tiles, NZ, fill, hi, runs);
   const double t_chunks = waves * (double(NZ) / chunks + fill);
-  const double t_seg = double(W) + double((W - 1) / NZ + 2) * fill;
-  return t_seg < 0.97 * t_chunks ? static_cast<int>(W) : 0;
+  return force || t_seg < 0.97 * t_chunks;
 }
 
 int prepare(wave_context* ctx, const wave_geometry* geom, float dt, int nt, int so, Prob* P) {
@@ -553,12 +600,8 @@ int prepare(wave_context* ctx, const wave_geometry* geom, float dt, int nt, int 
     int layout[kStepLayoutMax];
     const int per_sm = step_layout(P->R, nd, MODE_PLAIN, sp.iso != 0, layout) > 8 ? layout[8] : 2;
     const long long slots = static_cast<long long>(ctx->sm_count) * per_sm;
-    const int W = seg_planes_for(static_cast<long long>(tx) * ty, g.NZ, chunks, P->R, slots, ctx->col_segments == 2);
-    if (W > 0) {
-      const long long total = static_cast<long long>(tx) * ty * g.NZ;
-      P->seg_planes = W;
-      P->seg_ctas = static_cast<int>((total + W - 1) / W);
-    }
+    if (seg_plan(static_cast<long long>(tx) * ty, g.NZ, chunks, P->R, slots, ctx->col_segments == 2, &P->seg_runs))
+      P->seg_ctas = static_cast<int>(P->seg_runs.size()) - 1;
   }
   return WAVE_OK;
 }
@@ -934,8 +977,9 @@ int alloc_snapshots(wave_context* ctx, Prob& P, int fmt, int levels, SnapStore* 
 int seg_cell_lists(wave_context* ctx, const Prob& P, PointSetDev* ps, cudaStream_t s) {
   const int bx = step_bx(), by = step_by(P.R, P.ndim, P.sp.iso != 0);
   uint64_t key = 1469598103934665603ull;
-  const long long dims[7] = {P.seg_planes, P.seg_ctas, P.tiles_x, P.g.NZ, P.g.NY, P.g.pitch, by};
+  const long long dims[6] = {P.seg_ctas, P.tiles_x, P.g.NZ, P.g.NY, P.g.pitch, by};
   key = fnv(key, dims, sizeof(dims));
+  key = fnv(key, P.seg_runs.data(), P.seg_runs.size() * sizeof(long long));
   if (ps->seg_key == key && ps->seg_ptr) return WAVE_OK;
   const int ctas = P.seg_ctas;
   std::vector<int> owner(ps->cells_host.size());
@@ -947,7 +991,8 @@ int seg_cell_lists(wave_context* ctx, const Prob& P, PointSetDev* ps, cudaStream
     const int y = static_cast<int>(r % P.g.NY);
     const int z = static_cast<int>(r / P.g.NY);
     const long long col = static_cast<long long>(y / by) * P.tiles_x + x / bx;
-    owner[k] = static_cast<int>((col * P.g.NZ + z) / P.seg_planes);
+    const long long g = col * P.g.NZ + z;
+    owner[k] = static_cast<int>(std::upper_bound(P.seg_runs.begin(), P.seg_runs.end(), g) - P.seg_runs.begin()) - 1;
     ps->seg_ptr_h[owner[k] + 1]++;
   }
   for (int b = 0; b < ctas; ++b) ps->seg_ptr_h[b + 1] += ps->seg_ptr_h[b];
@@ -972,10 +1017,12 @@ int seg_cell_lists(wave_context* ctx, const Prob& P, PointSetDev* ps, cudaStream
 int forward_steps_seg(wave_context* ctx, Prob& P, Work& W, int n0, int n1, const float* q, PointSetDev* src,
                       float* d, PointSetDev* rec, cudaStream_t s) {
   SegWork w{};
-  w.seg_planes = P.seg_planes;
+  void* runs = nullptr;
+  TRY(ws_get(ctx, "seg_runs", P.seg_runs.size() * sizeof(long long), &runs));
+  CK(cudaMemcpyAsync(runs, P.seg_runs.data(), P.seg_runs.size() * sizeof(long long), cudaMemcpyHostToDevice, s));
+  w.run_start = static_cast<const long long*>(runs);
   w.tiles_x = P.tiles_x;
   w.tiles_y = P.tiles_y;
-  w.total = static_cast<long long>(P.tiles_x) * P.tiles_y * P.g.NZ;
   w.inj = inject_set(src);
   if (w.inj.n > 0) {
     TRY(seg_cell_lists(ctx, P, src, s));
@@ -2340,6 +2387,20 @@ int wave_storage_plan_for(int nt, size_t level_bytes, size_t field_bytes, size_t
   if (levels) *levels = plan.F;
   if (parts) *parts = plan.k;
   if (segments) *segments = plan.nseg;
+  return WAVE_OK;
+}
+
+int wave_column_runs_for(long long columns, int nz, int chunks, int space_order, long long slots, int force,
+                         long long* run_start, int cap, int* n_runs) {
+  if (columns < 1 || nz < 1 || chunks < 1 || slots < 1 || !valid_order(space_order) || !n_runs || cap < 0)
+    return WAVE_ERR_INVALID_ARG;
+  std::vector<long long> runs;
+  *n_runs = 0;
+  if (!seg_plan(columns, nz, chunks, space_order / 2, slots, force != 0, &runs)) return WAVE_OK;
+  const int n = static_cast<int>(runs.size()) - 1;
+  if (n + 1 > cap || !run_start) return WAVE_ERR_INVALID_ARG;
+  std::copy(runs.begin(), runs.end(), run_start);
+  *n_runs = n;
   return WAVE_OK;
 }
 

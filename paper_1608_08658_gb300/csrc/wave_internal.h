@@ -185,6 +185,13 @@ struct StepLayout {
   // phase flips once per group.
   static constexpr bool COMBINED = LEAD;
   static constexpr int UR = (COMBINED && UR_BASE > 1) ? nsu_of(LEAD, PF) : UR_BASE;
+  // Damped points on packed pairs (the same values as one point at a time)
+  // where measured faster on 592^3: the FP32 snapshot steps up to radius 4
+  // (order 8 0.640 -> 0.632 ms) and the 16-bit snapshot steps at radius 8
+  // (order 16 FP16 0.822 -> 0.795 ms); elsewhere the extra live pairs cost
+  // more than the halved arithmetic (order 16 forward 0.708 -> 0.728 ms).
+  static constexpr bool PACKED_DAMP =
+      (MODE == MODE_SNAP_F32 && R <= 4) || ((MODE == MODE_SNAP_BF16 || MODE == MODE_SNAP_F16) && R == 8);
   // resident CTAs per SM asked of the register allocator (registers per
   // thread follow the warps per SM sub-partition: 3 CTAs of 9 warps leave 72,
   // 2 of 9 leave 96, 2 of 8 leave 128)
@@ -327,16 +334,16 @@ struct BatchSparse {
 
 // Column segments of the plain 3D step, for grids of few CTA waves: the
 // tiles_x * tiles_y columns of NZ planes, tile after tile, form one sequence
-// of `total` planes, cut into runs of seg_planes, one run per CTA (a run may
-// end in one column and go on at the top of the next).  Such a launch also
-// does the step's sparse work: the injection of source row n into the cells
-// of the CTA's runs once its planes are written (inj_vals = row n, or null),
-// and the sampling of receiver row n from the centre level, a share of the
-// receivers per CTA, while its first planes load (rec_out = row n, or null).
+// of planes, cut into one run per CTA, [run_start[b], run_start[b+1]) for CTA
+// b (a run may end in one column and go on at the top of the next).  Such a
+// launch also does the step's sparse work: the injection of source row n into
+// the cells of the CTA's runs once its planes are written (inj_vals = row n,
+// or null), and the sampling of receiver row n from the centre level, a share
+// of the receivers per CTA, while its first planes load (rec_out = row n, or
+// null).
 struct SegWork {
-  int seg_planes;
+  const long long* run_start;  // [ctas + 1], device
   int tiles_x, tiles_y;
-  long long total;
   InjectSet inj;
   const int* inj_ptr;      // [ctas + 1]: the CTA's cells in inj_list
   const int* inj_list;     // indices into inj, grouped by CTA

@@ -70,6 +70,9 @@ _SIGS = {
     "wave_context_withhold_next_loads": (ctypes.c_int, [_P]),
     "wave_context_set_time_blocking": (ctypes.c_int, [_P, ctypes.c_int]),
     "wave_context_set_column_segments": (ctypes.c_int, [_P, ctypes.c_int]),
+    "wave_column_runs_for": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_longlong, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
+                                            ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "wave_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "wave_last_error": (ctypes.c_char_p, [_P]),
     "wave_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, ctypes.c_int, _P]),
@@ -595,6 +598,20 @@ def wave_step_kernel_layout(space_order, ndim, kernel, equal_spacing):
     if rc != WAVE_OK:
         raise WaveError(rc, "bad arguments to wave_step_kernel_layout")
     return dict(zip(STEP_LAYOUT_FIELDS, list(buf)[:n.value]))
+
+
+def wave_column_runs_for(columns, nz, chunks, space_order, slots=304, force=False):
+    """Host-only: run starts of the segmented plain step for a grid of
+    `columns` columns of nz planes (numpy int64 array of runs + 1 entries), or
+    None where the z chunks are kept."""
+    cap = int(min(slots, columns * nz)) + 1
+    buf = (ctypes.c_longlong * cap)()
+    n = ctypes.c_int()
+    rc = lib().wave_column_runs_for(int(columns), int(nz), int(chunks), int(space_order), int(slots),
+                                    int(bool(force)), buf, cap, ctypes.byref(n))
+    if rc != WAVE_OK:
+        raise WaveError(rc, "bad arguments to wave_column_runs_for")
+    return np.array(buf[:n.value + 1], dtype=np.int64) if n.value else None
 
 
 def wave_ricker(nt, dt, f0, t0=None, out=None):
