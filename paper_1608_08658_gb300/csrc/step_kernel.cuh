@@ -125,20 +125,23 @@ __device__ __forceinline__ void produce(const CUtensorMap& tm_u, const CUtensorM
   if (mode_is_grad(MODE)) prefetch_tensormap(&tm_s);
   bool ok = true;
   if constexpr (L::COMBINED) {
-    // one ring: stage s = queue box of plane z0 - RZ + s plus, from s = 2RZ
-    // on, the per-point tiles of plane s - 2RZ, under fullU/emptyU[s % NSU]
+    // one ring: stage s = queue box of plane z0 - RZ + S0 + s plus, from
+    // s = 2RZ - S0 on, the per-point tiles of plane s + S0 - 2RZ, under
+    // fullU/emptyU[s % NSU]; S0 = 2RZ where the consumers load the first 2RZ
+    // queue planes themselves (L::DIRECT_FILL), else 0
     constexpr int NS = L::NSU;
+    constexpr int S0 = L::DIRECT_FILL ? 2 * RZ : 0;
     static_assert(L::NSU == L::NSP, "one stage per plane for both rings");
     int issued = 0;
     for (int s = 0; s < nU; ++s) {
       const int slot = s % NS;
       if (s >= NS) ok = mbar_wait_bounded(&emptyU[slot], ((s / NS) - 1) & 1, abort_flag, p.wait_ns);
       if (!ok) break;
-      const bool tiles = s >= 2 * RZ;
+      const bool tiles = s + S0 >= 2 * RZ;
       mbar_arrive_expect_tx(&fullU[slot], L::Q_BYTES + (tiles ? L::P_TX : 0));
-      tma_load_4d(Ubase + slot * (L::Q_STRIDE / 4), &tm_p, x0, y0, z0 - RZ + s, p.cur, &fullU[slot]);
+      tma_load_4d(Ubase + slot * (L::Q_STRIDE / 4), &tm_p, x0, y0, z0 - RZ + S0 + s, p.cur, &fullU[slot]);
       if (tiles) {
-        const int j = s - 2 * RZ;
+        const int j = s + S0 - 2 * RZ;
         unsigned char* pd = Pbase + slot * L::P_BYTES;
         tma_load_4d(pd + L::HALO_OFF, &tm_u, x0 - L::HX, y0 - R, z0 + j, p.cur, &fullU[slot]);
         tma_load_4d(pd + L::PREV_OFF, &tm_p, x0, y0, z0 + j, p.prev, &fullU[slot]);
@@ -246,7 +249,7 @@ __device__ __forceinline__ void step_body(const CUtensorMap& tm_u, const CUtenso
   const int x0 = bx * T::BX;
   const int y0 = by * T::BY;
   const int nP = z1 - z0;
-  const int nU = nP + 2 * RZ;
+  const int nU = nP + (L::DIRECT_FILL ? 0 : 2 * RZ);  // stages the producer streams
   if (nP <= 0) return;
 
   if (tid == 0) {
@@ -334,18 +337,37 @@ __device__ __forceinline__ void step_body(const CUtensorMap& tm_u, const CUtenso
   for (int i = 0; i < NQ; ++i) q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 
   bool ok = true;
+  if constexpr (L::DIRECT_FILL) {
+    // the first 2RZ queue planes (z0 - RZ .. z0 + RZ - 1) straight from the
+    // centre level, all loads in flight at once: zero outside the grid like
+    // the tile loads' out-of-bounds fill (columns from NX to the pitch hold
+    // zeros in every field slot)
+    const float* cur = p.fields + p.cur * p.slot_elems;
+    const bool col = gy < p.NY && gx < p.pitch;
+    const long long plane = static_cast<long long>(p.NY) * p.pitch;
+    const long long at = static_cast<long long>(gy) * p.pitch + gx;
 #pragma unroll
-  for (int s = 0; s < 2 * RZ; ++s) {
-    const int slot = s % L::NSU;
-    ok = mbar_wait_bounded(&fullU[slot], (s / L::NSU) & 1, abort_flag, p.wait_ns);
-    ok = __all_sync(0xffffffffu, ok);
-    if (!ok) break;
-    q[s] = lds4(Ubase + slot * (L::Q_STRIDE / 4) + qofs);
-    if (L::LEAD || s < RZ) {
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&emptyU[slot]);
+    for (int s = 0; s < 2 * RZ; ++s) {
+      const int z = z0 - RZ + s;
+      q[s] = (col && z >= 0 && z < p.NZ) ? __ldg(reinterpret_cast<const float4*>(cur + z * plane + at))
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < 2 * RZ; ++s) {
+      const int slot = s % L::NSU;
+      ok = mbar_wait_bounded(&fullU[slot], (s / L::NSU) & 1, abort_flag, p.wait_ns);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      q[s] = lds4(Ubase + slot * (L::Q_STRIDE / 4) + qofs);
+      if (L::LEAD || s < RZ) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&emptyU[slot]);
+      }
     }
   }
+  // ring sequence of output plane 0's stage
+  constexpr int S0 = L::DIRECT_FILL ? 0 : 2 * RZ;
 
   const long long plane_elems = static_cast<long long>(p.NY) * p.pitch;
   long long idx = static_cast<long long>(z0) * plane_elems + static_cast<long long>(gy) * p.pitch + gx;
@@ -360,10 +382,10 @@ __device__ __forceinline__ void step_body(const CUtensorMap& tm_u, const CUtenso
   }
   float* const out_base = p.fields + p.prev * p.slot_elems;
   int j = 0;
-  // ring positions of output plane j: plane z+R has sequence j+2RZ in the
-  // queue-feed ring, the centre plane j+RZ, the per-point tiles j
-  int ring_un = (2 * RZ) % L::NSU, ring_ps = 0;
-  uint32_t phase_un = ((2 * RZ) / L::NSU) & 1, phase_ps = 0;
+  // ring positions of output plane j: plane z+R has sequence j+S0 in the
+  // queue-feed ring, the centre plane j+S0-RZ, the per-point tiles j
+  int ring_un = S0 % L::NSU, ring_ps = 0;
+  uint32_t phase_un = (S0 / L::NSU) & 1, phase_ps = 0;
 
   // One output plane z = z0 + j, taking its queue entries at offset O of a
   // window renamed by PH (entry i at q[(PH + O + i) % NQ]).
@@ -618,8 +640,8 @@ __device__ __forceinline__ void step_body(const CUtensorMap& tm_u, const CUtenso
     uint32_t gpar = 0;
     auto renamed = [&](auto phc) -> bool {
       constexpr int u = decltype(phc)::value;
-      constexpr int sl = (2 * RZ + u) % L::NSU;
-      const uint32_t par = gpar ^ static_cast<uint32_t>(((2 * RZ + u) / L::NSU) & 1);
+      constexpr int sl = (S0 + u) % L::NSU;
+      const uint32_t par = gpar ^ static_cast<uint32_t>(((S0 + u) / L::NSU) & 1);
       if (!plane(IntC<0>{}, phc, sl, par, sl, par)) return false;
       ++j;
       idx += plane_elems;
@@ -637,8 +659,8 @@ __device__ __forceinline__ void step_body(const CUtensorMap& tm_u, const CUtenso
         for (int i = 0; i < NQ; ++i) q[i] = t[i];
       }
     }
-    ring_un = (j + 2 * RZ) % L::NSU;
-    phase_un = ((j + 2 * RZ) / L::NSU) & 1;
+    ring_un = (j + S0) % L::NSU;
+    phase_un = ((j + S0) / L::NSU) & 1;
   } else if constexpr (UR > 1) {
     auto renamed = [&](auto phc) -> bool {
       if (!ring(IntC<0>{}, phc)) return false;

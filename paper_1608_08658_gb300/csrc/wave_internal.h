@@ -184,6 +184,11 @@ struct StepLayout {
   // so that within a group every stage slot is a compile-time offset and the
   // phase flips once per group.
   static constexpr bool COMBINED = LEAD;
+  // One-ring kernels: the consumers load the first 2RZ queue planes of a
+  // column run themselves (independent 16-byte loads, all in flight) instead
+  // of taking them through the ring a few stages at a time; the ring starts at
+  // output plane 0.
+  static constexpr bool DIRECT_FILL = COMBINED;
   static constexpr int UR = (COMBINED && UR_BASE > 1) ? nsu_of(LEAD, PF) : UR_BASE;
   // Damped points on packed pairs (the same values as one point at a time)
   // where measured faster on 592^3: the FP32 snapshot steps up to radius 4
