@@ -98,7 +98,7 @@ __device__ __forceinline__ bool call_in_order(F& f, IntC<I>, IntC<N>) {
   }
 }
 
-// Producer warp of a step kernel (layout L: StepLayout or TallLayout).  Lane
+// Producer warp of a step kernel (layout L: StepLayout or Step2Layout).  Lane
 // 0 streams the CTA's planes through the two rings: the queue-feed stage of
 // sequence s (the centre-level halo plane z0 - RZ + s, or in the lead-plane
 // layout its interior box) and, from s = 2 RZ on, the per-point stage of plane
@@ -747,10 +747,10 @@ __device__ __forceinline__ void sample_share(const GatherSet& gs, const float* _
 }
 
 // Segmented plain step (3D, SegWork): CTA b computes its run of the tile-major
-// column sequence, one step body per column it touches (the
-// ring barriers are ended and initialised again in between), samples its share
-// of the receivers from the centre level during its first segment, and then
-// injects source row n into the cells of its segments.
+// column sequence, one step body per column it touches (the ring barriers are
+// ended and initialised again in between), samples its share of the receivers
+// from the centre level during its first segment, and then injects source row
+// n into the cells of its segments.
 template <int R, bool ISO>
 __global__ void __launch_bounds__(StepTraits<R, 3, ISO>::NTHREADS, (StepLayout<R, 3, MODE_PLAIN, ISO>::MIN_BLOCKS))
     step_seg_kernel(const __grid_constant__ CUtensorMap tm_u, const __grid_constant__ CUtensorMap tm_p,
