@@ -971,21 +971,15 @@ int alloc_snapshots(wave_context* ctx, Prob& P, int fmt, int levels, SnapStore* 
   return snapshot_map(ctx, P, fmt, S->data, levels, &S->map);
 }
 
-// Cells of an injection set per CTA of the segmented step (CSR over the
-// CTAs, device copies in the workspace), kept on the point set for the
-// decomposition they were made for.
-int seg_cell_lists(wave_context* ctx, const Prob& P, PointSetDev* ps, cudaStream_t s) {
+// Cells of an injection set per CTA of the segmented step: CSR over the
+// CTAs (ptr, ctas + 1 entries) of indices into the set's cells (list).
+void seg_cell_csr(const Prob& P, const std::vector<long long>& cells, std::vector<int>* ptr, std::vector<int>* list) {
   const int bx = step_bx(), by = step_by(P.R, P.ndim, P.sp.iso != 0);
-  uint64_t key = 1469598103934665603ull;
-  const long long dims[6] = {P.seg_ctas, P.tiles_x, P.g.NZ, P.g.NY, P.g.pitch, by};
-  key = fnv(key, dims, sizeof(dims));
-  key = fnv(key, P.seg_runs.data(), P.seg_runs.size() * sizeof(long long));
-  if (ps->seg_key == key && ps->seg_ptr) return WAVE_OK;
   const int ctas = P.seg_ctas;
-  std::vector<int> owner(ps->cells_host.size());
-  ps->seg_ptr_h.assign(static_cast<size_t>(ctas) + 1, 0);
+  std::vector<int> owner(cells.size());
+  ptr->assign(static_cast<size_t>(ctas) + 1, 0);
   for (size_t k = 0; k < owner.size(); ++k) {
-    const long long c = ps->cells_host[k];
+    const long long c = cells[k];
     const int x = static_cast<int>(c % P.g.pitch);
     const long long r = c / P.g.pitch;
     const int y = static_cast<int>(r % P.g.NY);
@@ -993,12 +987,26 @@ int seg_cell_lists(wave_context* ctx, const Prob& P, PointSetDev* ps, cudaStream
     const long long col = static_cast<long long>(y / by) * P.tiles_x + x / bx;
     const long long g = col * P.g.NZ + z;
     owner[k] = static_cast<int>(std::upper_bound(P.seg_runs.begin(), P.seg_runs.end(), g) - P.seg_runs.begin()) - 1;
-    ps->seg_ptr_h[owner[k] + 1]++;
+    (*ptr)[owner[k] + 1]++;
   }
-  for (int b = 0; b < ctas; ++b) ps->seg_ptr_h[b + 1] += ps->seg_ptr_h[b];
-  ps->seg_list_h.assign(std::max<size_t>(1, owner.size()), 0);
-  std::vector<int> fill(ps->seg_ptr_h.begin(), ps->seg_ptr_h.end() - 1);
-  for (size_t k = 0; k < owner.size(); ++k) ps->seg_list_h[fill[owner[k]]++] = static_cast<int>(k);
+  for (int b = 0; b < ctas; ++b) (*ptr)[b + 1] += (*ptr)[b];
+  list->assign(std::max<size_t>(1, owner.size()), 0);
+  std::vector<int> fill(ptr->begin(), ptr->end() - 1);
+  for (size_t k = 0; k < owner.size(); ++k) (*list)[fill[owner[k]]++] = static_cast<int>(k);
+}
+
+// The same lists for a point set cached in the context (device copies in the
+// context's workspace, kept on the point set for the decomposition they were
+// made for).  Calls on a context run one after another, so its workspace
+// serves them; resident sessions keep their own copies (SegBuffers).
+int seg_cell_lists(wave_context* ctx, const Prob& P, PointSetDev* ps, cudaStream_t s) {
+  const int by = step_by(P.R, P.ndim, P.sp.iso != 0);
+  uint64_t key = 1469598103934665603ull;
+  const long long dims[6] = {P.seg_ctas, P.tiles_x, P.g.NZ, P.g.NY, P.g.pitch, by};
+  key = fnv(key, dims, sizeof(dims));
+  key = fnv(key, P.seg_runs.data(), P.seg_runs.size() * sizeof(long long));
+  if (ps->seg_key == key && ps->seg_ptr) return WAVE_OK;
+  seg_cell_csr(P, ps->cells_host, &ps->seg_ptr_h, &ps->seg_list_h);
   void* p = nullptr;
   TRY(ws_get(ctx, ps->tag + "segptr", ps->seg_ptr_h.size() * 4, &p));
   ps->seg_ptr = static_cast<int*>(p);
@@ -1011,24 +1019,39 @@ int seg_cell_lists(wave_context* ctx, const Prob& P, PointSetDev* ps, cudaStream
   return WAVE_OK;
 }
 
+// Device copies of a decomposition's run starts and of a source set's cell
+// lists, owned by whoever enqueues the launches that read them.
+struct SegBuffers {
+  const long long* runs = nullptr;
+  const int* inj_ptr = nullptr;
+  const int* inj_list = nullptr;
+};
+
 // Plain forward steps n = n0 .. n1-1 by the segmented step: step n injects
 // row n of q into level n+1 and samples receiver row n from level n (n > n0);
 // row n1 is sampled after the last step.
 int forward_steps_seg(wave_context* ctx, Prob& P, Work& W, int n0, int n1, const float* q, PointSetDev* src,
-                      float* d, PointSetDev* rec, cudaStream_t s) {
+                      float* d, PointSetDev* rec, cudaStream_t s, const SegBuffers* own = nullptr) {
   SegWork w{};
-  void* runs = nullptr;
-  TRY(ws_get(ctx, "seg_runs", P.seg_runs.size() * sizeof(long long), &runs));
-  CK(cudaMemcpyAsync(runs, P.seg_runs.data(), P.seg_runs.size() * sizeof(long long), cudaMemcpyHostToDevice, s));
-  w.run_start = static_cast<const long long*>(runs);
+  w.inj = inject_set(src);
+  if (own) {
+    // a resident session's copies: no other caller writes them
+    w.run_start = own->runs;
+    w.inj_ptr = own->inj_ptr;
+    w.inj_list = own->inj_list;
+  } else {
+    void* runs = nullptr;
+    TRY(ws_get(ctx, "seg_runs", P.seg_runs.size() * sizeof(long long), &runs));
+    CK(cudaMemcpyAsync(runs, P.seg_runs.data(), P.seg_runs.size() * sizeof(long long), cudaMemcpyHostToDevice, s));
+    w.run_start = static_cast<const long long*>(runs);
+    if (w.inj.n > 0) {
+      TRY(seg_cell_lists(ctx, P, src, s));
+      w.inj_ptr = src->seg_ptr;
+      w.inj_list = src->seg_list;
+    }
+  }
   w.tiles_x = P.tiles_x;
   w.tiles_y = P.tiles_y;
-  w.inj = inject_set(src);
-  if (w.inj.n > 0) {
-    TRY(seg_cell_lists(ctx, P, src, s));
-    w.inj_ptr = src->seg_ptr;
-    w.inj_list = src->seg_list;
-  }
   const bool sample = rec && rec->n > 0 && d;
   if (sample) w.rec = gather_set(P, rec);
   for (int n = n0; n < n1; ++n) {
@@ -1653,8 +1676,12 @@ int gradient_impl(wave_context* ctx, const wave_geometry* geom, const float* m, 
 // data, point structures, the step counter.
 size_t session_bytes(const Prob& P, const PointsHost& hs, const PointsHost& hr, long long ns, long long nr) {
   auto r = [](size_t b) { return round_up(std::max<size_t>(b, 256), 256); };
+  // the segmented step's run starts and the sources' cell lists per CTA
+  const size_t seg = P.seg_ctas > 0 ? r(P.seg_runs.size() * 8) + r((static_cast<size_t>(P.seg_ctas) + 1) * 4) +
+                                          r(std::max<size_t>(1, hs.cells.size()) * 4)
+                                    : 0;
   return r(2 * P.slot_elems * 4) + r(P.slot_elems * 4) + r(P.phys_elems * 4) + r(static_cast<size_t>(P.nt) * ns * 4) +
-         r(static_cast<size_t>(P.nt) * nr * 4) + points_device_bytes(hs) + points_device_bytes(hr) + r(4);
+         r(static_cast<size_t>(P.nt) * nr * 4) + points_device_bytes(hs) + points_device_bytes(hr) + r(4) + seg;
 }
 
 }  // namespace
@@ -1674,6 +1701,9 @@ struct wave_session {
   int chunk = 0;     // steps per captured graph (even)
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t done = nullptr;
+  // the segmented step's buffers for the steps outside captured chunks (the
+  // session's own: other sessions enqueue on other streams meanwhile)
+  SegBuffers seg;
 };
 
 namespace {
@@ -1808,6 +1838,20 @@ int session_create_impl(wave_context* ctx, wave_session* S, const wave_geometry*
   if (S->ns > 0) CK(cudaMemcpyAsync(S->q, q, static_cast<size_t>(nt) * S->ns * 4, cudaMemcpyDefault, s));
   TRY(sess_points(S, hs, &S->src));
   TRY(sess_points(S, hr, &S->rec));
+  if (P.seg_ctas > 0) {
+    std::vector<int> ptr, list;
+    seg_cell_csr(P, hs.cells, &ptr, &list);
+    TRY(sess_alloc(S, P.seg_runs.size() * 8, &p));
+    CK(cudaMemcpyAsync(p, P.seg_runs.data(), P.seg_runs.size() * 8, cudaMemcpyHostToDevice, s));
+    S->seg.runs = static_cast<const long long*>(p);
+    TRY(sess_alloc(S, ptr.size() * 4, &p));
+    CK(cudaMemcpyAsync(p, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice, s));
+    S->seg.inj_ptr = static_cast<const int*>(p);
+    TRY(sess_alloc(S, list.size() * 4, &p));
+    CK(cudaMemcpyAsync(p, list.data(), list.size() * 4, cudaMemcpyHostToDevice, s));
+    S->seg.inj_list = static_cast<const int*>(p);
+    CK(cudaStreamSynchronize(s));  // the host vectors end with this scope
+  }
   TRY(setup_model(ctx, P, md, cm, s));
   TRY(make_field_maps(ctx, P, fields, 2, cm, nullptr, &S->W));
   TRY(inject_coefficients(ctx, P, S->W, &S->src, s));
@@ -2179,8 +2223,12 @@ int wave_session_advance(wave_session* S, int steps, int* steps_left) {
       // steps that do not fill a whole captured chunk (the tail, or every
       // step when no graph was captured) run as ordinary launches
       const int stop = std::min(total, S->next + std::max(steps, 1));
-      TRY(forward_steps(ctx, P, S->W, S->next, stop, S->q, &S->src, S->d, S->nr > 0 ? &S->rec : nullptr, nullptr,
-                        0, 0, s));
+      if (P.seg_ctas > 0)
+        TRY(forward_steps_seg(ctx, P, S->W, S->next, stop, S->q, &S->src, S->d, S->nr > 0 ? &S->rec : nullptr, s,
+                              &S->seg));
+      else
+        TRY(forward_steps(ctx, P, S->W, S->next, stop, S->q, &S->src, S->d, S->nr > 0 ? &S->rec : nullptr,
+                          nullptr, 0, 0, s));
       steps -= stop - S->next;
       S->next = stop;
     }
