@@ -1028,10 +1028,11 @@ struct SegBuffers {
 };
 
 // Plain forward steps n = n0 .. n1-1 by the segmented step: step n injects
-// row n of q into level n+1 and samples receiver row n from level n (n > n0);
-// row n1 is sampled after the last step.
+// row n of q into level n+1 and samples receiver row n from level n (n > n0,
+// or n >= n0 with sample_first); row n1 is sampled after the last step.
 int forward_steps_seg(wave_context* ctx, Prob& P, Work& W, int n0, int n1, const float* q, PointSetDev* src,
-                      float* d, PointSetDev* rec, cudaStream_t s, const SegBuffers* own = nullptr) {
+                      float* d, PointSetDev* rec, cudaStream_t s, const SegBuffers* own = nullptr,
+                      bool sample_first = false) {
   SegWork w{};
   w.inj = inject_set(src);
   if (own) {
@@ -1063,7 +1064,7 @@ int forward_steps_seg(wave_context* ctx, Prob& P, Work& W, int n0, int n1, const
       ctx->withhold_next = false;
     }
     w.inj_vals = w.inj.n > 0 ? q + static_cast<long long>(n) * src->n : nullptr;
-    w.rec_out = sample && n > n0 ? d + static_cast<long long>(n) * rec->n : nullptr;
+    w.rec_out = sample && (n > n0 || sample_first) ? d + static_cast<long long>(n) * rec->n : nullptr;
     TRY(launch(ctx, WAVE_KERNEL_STEP, s,
                [&] { return launch_step_seg(P.R, sp.iso != 0, W.maps, sp, w, P.seg_ctas, s); }));
   }
@@ -1760,6 +1761,34 @@ int enqueue_chunk_body(wave_session* S, int count, cudaStream_t s) {
   Prob& P = S->P;
   InjectSet isrc = inject_set(&S->src);
   GatherSet grec = gather_set(P, &S->rec);
+  if (P.seg_ctas > 0) {
+    // one segmented step per time step: step i of the chunk injects row
+    // counter + i into its new level and samples row counter + i from its
+    // centre level (row counter + count is left to the next steps)
+    SegWork w{};
+    w.run_start = S->seg.runs;
+    w.tiles_x = P.tiles_x;
+    w.tiles_y = P.tiles_y;
+    w.inj = isrc;
+    w.inj_ptr = S->seg.inj_ptr;
+    w.inj_list = S->seg.inj_list;
+    w.inj_vals = isrc.n > 0 ? S->q : nullptr;
+    w.inj_stride = S->ns;
+    w.rec = grec;
+    w.rec_out = S->nr > 0 ? S->d : nullptr;
+    w.rec_stride = S->nr;
+    w.row_counter = S->counter;
+    for (int i = 0; i < count; ++i) {
+      P.sp.cur = fslot(i);
+      P.sp.prev = fslot(i - 1);
+      w.row_offset = i;
+      cudaError_t e = launch_step_seg(P.R, P.sp.iso != 0, S->W.maps, P.sp, w, P.seg_ctas, s);
+      if (e != cudaSuccess) return fail(ctx, WAVE_ERR_CUDA, "launch during capture failed: %s", cudaGetErrorString(e));
+    }
+    cudaError_t e = launch_counter_add(S->counter, count, s);
+    if (e != cudaSuccess) return fail(ctx, WAVE_ERR_CUDA, "launch during capture failed: %s", cudaGetErrorString(e));
+    return WAVE_OK;
+  }
   for (int i = 0; i < count; ++i) {
     P.sp.cur = fslot(i);
     P.sp.prev = fslot(i - 1);
@@ -2215,17 +2244,25 @@ int wave_session_advance(wave_session* S, int steps, int* steps_left) {
     if (S->exec && S->next % S->chunk == 0 && total - S->next >= S->chunk) {
       CK(cudaGraphLaunch(S->exec, s));
       ctx->launches[WAVE_KERNEL_STEP] += S->chunk;
-      ctx->launches[WAVE_KERNEL_SPARSE] += 2 * S->chunk;
+      ctx->launches[WAVE_KERNEL_SPARSE] += P.seg_ctas > 0 ? 0 : 2 * S->chunk;
       ctx->launches[WAVE_KERNEL_OTHER] += 1;
       S->next += S->chunk;
       steps -= S->chunk;
+      if (P.seg_ctas > 0 && S->next == total && S->nr > 0) {
+        // the captured segmented steps leave the last row to the next step
+        GatherSet grec = gather_set(P, &S->rec);
+        float* row = S->d + static_cast<long long>(total) * S->nr;
+        const float* level = slot_ptr(S->W, P, fslot(total));
+        TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_gather(grec, level, row, s); }));
+      }
     } else {
       // steps that do not fill a whole captured chunk (the tail, or every
       // step when no graph was captured) run as ordinary launches
       const int stop = std::min(total, S->next + std::max(steps, 1));
       if (P.seg_ctas > 0)
+        // after a captured chunk of segmented steps row S->next is still to be sampled
         TRY(forward_steps_seg(ctx, P, S->W, S->next, stop, S->q, &S->src, S->d, S->nr > 0 ? &S->rec : nullptr, s,
-                              &S->seg));
+                              &S->seg, S->exec != nullptr && S->next > 0));
       else
         TRY(forward_steps(ctx, P, S->W, S->next, stop, S->q, &S->src, S->d, S->nr > 0 ? &S->rec : nullptr,
                           nullptr, 0, 0, s));
