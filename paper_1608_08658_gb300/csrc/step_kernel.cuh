@@ -760,17 +760,13 @@ __global__ void __launch_bounds__(StepTraits<R, 3, ISO>::NTHREADS, (StepLayout<R
   using L = StepLayout<R, 3, MODE_PLAIN, ISO>;
   const long long g0 = w.run_start[blockIdx.x];
   const long long g1 = w.run_start[blockIdx.x + 1];
-  // this step's rows of the source and receiver traces
-  const long long n_row = w.row_counter ? static_cast<long long>(*w.row_counter + w.row_offset) : 0;
-  const float* inj_vals = w.inj_vals ? w.inj_vals + n_row * w.inj_stride : nullptr;
-  float* rec_out = w.rec_out ? w.rec_out + n_row * w.rec_stride : nullptr;
   bool first = true;
   auto pre = [&](int ctid) {
-    if (!first || rec_out == nullptr) return;
+    if (!first || w.rec_out == nullptr) return;
     const long long share = (w.rec.n + gridDim.x - 1) / gridDim.x;
     const long long r0 = min(static_cast<long long>(blockIdx.x) * share, w.rec.n);
     const long long r1 = min(r0 + share, w.rec.n);
-    sample_share<T::NCW, (T::NCW == 8 && R >= 5) ? 4 : 8>(w.rec, p.fields + p.cur * p.slot_elems, rec_out, r0, r1, ctid);
+    sample_share<T::NCW, (T::NCW == 8 && R >= 5) ? 4 : 8>(w.rec, p.fields + p.cur * p.slot_elems, w.rec_out, r0, r1, ctid);
   };
   for (long long g = g0; g < g1;) {
     const long long col = g / p.NZ;
@@ -791,7 +787,7 @@ __global__ void __launch_bounds__(StepTraits<R, 3, ISO>::NTHREADS, (StepLayout<R
     first = false;
     g += z1 - z0;
   }
-  if (inj_vals == nullptr) return;
+  if (w.inj_vals == nullptr) return;
   // the new level of the CTA's cells is written; the arithmetic of inject_kernel
   __syncthreads();
   float* field = p.fields + p.prev * p.slot_elems;
@@ -799,7 +795,7 @@ __global__ void __launch_bounds__(StepTraits<R, 3, ISO>::NTHREADS, (StepLayout<R
        e += blockDim.x) {
     const int k = w.inj_list[e];
     float s = 0.f;
-    for (int i = w.inj.rowptr[k]; i < w.inj.rowptr[k + 1]; ++i) s = fmaf(w.inj.w[i], inj_vals[w.inj.pidx[i]], s);
+    for (int i = w.inj.rowptr[k]; i < w.inj.rowptr[k + 1]; ++i) s = fmaf(w.inj.w[i], w.inj_vals[w.inj.pidx[i]], s);
     field[w.inj.cell[k]] = fmaf(w.inj.coef[k], s, field[w.inj.cell[k]]);
   }
 }

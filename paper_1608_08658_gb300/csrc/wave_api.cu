@@ -997,8 +997,9 @@ void seg_cell_csr(const Prob& P, const std::vector<long long>& cells, std::vecto
 
 // The same lists for a point set cached in the context (device copies in the
 // context's workspace, kept on the point set for the decomposition they were
-// made for).  Calls on a context run one after another, so its workspace
-// serves them; resident sessions keep their own copies (SegBuffers).
+// made for).  Calls on a context run one after another and return after their
+// stream completes, so its workspace serves them (resident sessions, whose
+// launches stay queued on their own streams, never take the segmented step).
 int seg_cell_lists(wave_context* ctx, const Prob& P, PointSetDev* ps, cudaStream_t s) {
   const int by = step_by(P.R, P.ndim, P.sp.iso != 0);
   uint64_t key = 1469598103934665603ull;
@@ -1019,37 +1020,21 @@ int seg_cell_lists(wave_context* ctx, const Prob& P, PointSetDev* ps, cudaStream
   return WAVE_OK;
 }
 
-// Device copies of a decomposition's run starts and of a source set's cell
-// lists, owned by whoever enqueues the launches that read them.
-struct SegBuffers {
-  const long long* runs = nullptr;
-  const int* inj_ptr = nullptr;
-  const int* inj_list = nullptr;
-};
-
 // Plain forward steps n = n0 .. n1-1 by the segmented step: step n injects
-// row n of q into level n+1 and samples receiver row n from level n (n > n0,
-// or n >= n0 with sample_first); row n1 is sampled after the last step.
+// row n of q into level n+1 and samples receiver row n from level n (n > n0);
+// row n1 is sampled after the last step.
 int forward_steps_seg(wave_context* ctx, Prob& P, Work& W, int n0, int n1, const float* q, PointSetDev* src,
-                      float* d, PointSetDev* rec, cudaStream_t s, const SegBuffers* own = nullptr,
-                      bool sample_first = false) {
+                      float* d, PointSetDev* rec, cudaStream_t s) {
   SegWork w{};
   w.inj = inject_set(src);
-  if (own) {
-    // a resident session's copies: no other caller writes them
-    w.run_start = own->runs;
-    w.inj_ptr = own->inj_ptr;
-    w.inj_list = own->inj_list;
-  } else {
-    void* runs = nullptr;
-    TRY(ws_get(ctx, "seg_runs", P.seg_runs.size() * sizeof(long long), &runs));
-    CK(cudaMemcpyAsync(runs, P.seg_runs.data(), P.seg_runs.size() * sizeof(long long), cudaMemcpyHostToDevice, s));
-    w.run_start = static_cast<const long long*>(runs);
-    if (w.inj.n > 0) {
-      TRY(seg_cell_lists(ctx, P, src, s));
-      w.inj_ptr = src->seg_ptr;
-      w.inj_list = src->seg_list;
-    }
+  void* runs = nullptr;
+  TRY(ws_get(ctx, "seg_runs", P.seg_runs.size() * sizeof(long long), &runs));
+  CK(cudaMemcpyAsync(runs, P.seg_runs.data(), P.seg_runs.size() * sizeof(long long), cudaMemcpyHostToDevice, s));
+  w.run_start = static_cast<const long long*>(runs);
+  if (w.inj.n > 0) {
+    TRY(seg_cell_lists(ctx, P, src, s));
+    w.inj_ptr = src->seg_ptr;
+    w.inj_list = src->seg_list;
   }
   w.tiles_x = P.tiles_x;
   w.tiles_y = P.tiles_y;
@@ -1064,7 +1049,7 @@ int forward_steps_seg(wave_context* ctx, Prob& P, Work& W, int n0, int n1, const
       ctx->withhold_next = false;
     }
     w.inj_vals = w.inj.n > 0 ? q + static_cast<long long>(n) * src->n : nullptr;
-    w.rec_out = sample && (n > n0 || sample_first) ? d + static_cast<long long>(n) * rec->n : nullptr;
+    w.rec_out = sample && n > n0 ? d + static_cast<long long>(n) * rec->n : nullptr;
     TRY(launch(ctx, WAVE_KERNEL_STEP, s,
                [&] { return launch_step_seg(P.R, sp.iso != 0, W.maps, sp, w, P.seg_ctas, s); }));
   }
@@ -1677,12 +1662,19 @@ int gradient_impl(wave_context* ctx, const wave_geometry* geom, const float* m, 
 // data, point structures, the step counter.
 size_t session_bytes(const Prob& P, const PointsHost& hs, const PointsHost& hr, long long ns, long long nr) {
   auto r = [](size_t b) { return round_up(std::max<size_t>(b, 256), 256); };
-  // the segmented step's run starts and the sources' cell lists per CTA
-  const size_t seg = P.seg_ctas > 0 ? r(P.seg_runs.size() * 8) + r((static_cast<size_t>(P.seg_ctas) + 1) * 4) +
-                                          r(std::max<size_t>(1, hs.cells.size()) * 4)
-                                    : 0;
   return r(2 * P.slot_elems * 4) + r(P.slot_elems * 4) + r(P.phys_elems * 4) + r(static_cast<size_t>(P.nt) * ns * 4) +
-         r(static_cast<size_t>(P.nt) * nr * 4) + points_device_bytes(hs) + points_device_bytes(hr) + r(4) + seg;
+         r(static_cast<size_t>(P.nt) * nr * 4) + points_device_bytes(hs) + points_device_bytes(hr) + r(4);
+}
+
+// Resident sessions share the GPU with one another: the z chunks of one
+// request's steps fill the waves another request leaves idle, and the column
+// segments' cost model (one kernel alone on the GPU) does not apply.  Measured
+// with the 600-request served stream: 11.9 shots/s with z chunks against 9.9 -
+// 11.4 with segments.  So sessions keep the z-chunk grid, with the separate
+// injection and sampling launches, for every step.
+void session_grid(Prob* P) {
+  P->seg_ctas = 0;
+  P->seg_runs.clear();
 }
 
 }  // namespace
@@ -1702,9 +1694,6 @@ struct wave_session {
   int chunk = 0;     // steps per captured graph (even)
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t done = nullptr;
-  // the segmented step's buffers for the steps outside captured chunks (the
-  // session's own: other sessions enqueue on other streams meanwhile)
-  SegBuffers seg;
 };
 
 namespace {
@@ -1761,34 +1750,6 @@ int enqueue_chunk_body(wave_session* S, int count, cudaStream_t s) {
   Prob& P = S->P;
   InjectSet isrc = inject_set(&S->src);
   GatherSet grec = gather_set(P, &S->rec);
-  if (P.seg_ctas > 0) {
-    // one segmented step per time step: step i of the chunk injects row
-    // counter + i into its new level and samples row counter + i from its
-    // centre level (row counter + count is left to the next steps)
-    SegWork w{};
-    w.run_start = S->seg.runs;
-    w.tiles_x = P.tiles_x;
-    w.tiles_y = P.tiles_y;
-    w.inj = isrc;
-    w.inj_ptr = S->seg.inj_ptr;
-    w.inj_list = S->seg.inj_list;
-    w.inj_vals = isrc.n > 0 ? S->q : nullptr;
-    w.inj_stride = S->ns;
-    w.rec = grec;
-    w.rec_out = S->nr > 0 ? S->d : nullptr;
-    w.rec_stride = S->nr;
-    w.row_counter = S->counter;
-    for (int i = 0; i < count; ++i) {
-      P.sp.cur = fslot(i);
-      P.sp.prev = fslot(i - 1);
-      w.row_offset = i;
-      cudaError_t e = launch_step_seg(P.R, P.sp.iso != 0, S->W.maps, P.sp, w, P.seg_ctas, s);
-      if (e != cudaSuccess) return fail(ctx, WAVE_ERR_CUDA, "launch during capture failed: %s", cudaGetErrorString(e));
-    }
-    cudaError_t e = launch_counter_add(S->counter, count, s);
-    if (e != cudaSuccess) return fail(ctx, WAVE_ERR_CUDA, "launch during capture failed: %s", cudaGetErrorString(e));
-    return WAVE_OK;
-  }
   for (int i = 0; i < count; ++i) {
     P.sp.cur = fslot(i);
     P.sp.prev = fslot(i - 1);
@@ -1842,6 +1803,7 @@ int session_create_impl(wave_context* ctx, wave_session* S, const wave_geometry*
   TRY(check_common(ctx, geom, m));
   Prob& P = S->P;
   TRY(prepare(ctx, geom, dt, nt, so, &P));
+  session_grid(&P);
   wave_points empty{0, nullptr};
   PointsHost hs, hr;
   TRY(build_points_host(ctx, P, src ? src : &empty, &hs));
@@ -1867,20 +1829,6 @@ int session_create_impl(wave_context* ctx, wave_session* S, const wave_geometry*
   if (S->ns > 0) CK(cudaMemcpyAsync(S->q, q, static_cast<size_t>(nt) * S->ns * 4, cudaMemcpyDefault, s));
   TRY(sess_points(S, hs, &S->src));
   TRY(sess_points(S, hr, &S->rec));
-  if (P.seg_ctas > 0) {
-    std::vector<int> ptr, list;
-    seg_cell_csr(P, hs.cells, &ptr, &list);
-    TRY(sess_alloc(S, P.seg_runs.size() * 8, &p));
-    CK(cudaMemcpyAsync(p, P.seg_runs.data(), P.seg_runs.size() * 8, cudaMemcpyHostToDevice, s));
-    S->seg.runs = static_cast<const long long*>(p);
-    TRY(sess_alloc(S, ptr.size() * 4, &p));
-    CK(cudaMemcpyAsync(p, ptr.data(), ptr.size() * 4, cudaMemcpyHostToDevice, s));
-    S->seg.inj_ptr = static_cast<const int*>(p);
-    TRY(sess_alloc(S, list.size() * 4, &p));
-    CK(cudaMemcpyAsync(p, list.data(), list.size() * 4, cudaMemcpyHostToDevice, s));
-    S->seg.inj_list = static_cast<const int*>(p);
-    CK(cudaStreamSynchronize(s));  // the host vectors end with this scope
-  }
   TRY(setup_model(ctx, P, md, cm, s));
   TRY(make_field_maps(ctx, P, fields, 2, cm, nullptr, &S->W));
   TRY(inject_coefficients(ctx, P, S->W, &S->src, s));
@@ -2244,28 +2192,16 @@ int wave_session_advance(wave_session* S, int steps, int* steps_left) {
     if (S->exec && S->next % S->chunk == 0 && total - S->next >= S->chunk) {
       CK(cudaGraphLaunch(S->exec, s));
       ctx->launches[WAVE_KERNEL_STEP] += S->chunk;
-      ctx->launches[WAVE_KERNEL_SPARSE] += P.seg_ctas > 0 ? 0 : 2 * S->chunk;
+      ctx->launches[WAVE_KERNEL_SPARSE] += 2 * S->chunk;
       ctx->launches[WAVE_KERNEL_OTHER] += 1;
       S->next += S->chunk;
       steps -= S->chunk;
-      if (P.seg_ctas > 0 && S->next == total && S->nr > 0) {
-        // the captured segmented steps leave the last row to the next step
-        GatherSet grec = gather_set(P, &S->rec);
-        float* row = S->d + static_cast<long long>(total) * S->nr;
-        const float* level = slot_ptr(S->W, P, fslot(total));
-        TRY(launch(ctx, WAVE_KERNEL_SPARSE, s, [&] { return launch_gather(grec, level, row, s); }));
-      }
     } else {
       // steps that do not fill a whole captured chunk (the tail, or every
       // step when no graph was captured) run as ordinary launches
       const int stop = std::min(total, S->next + std::max(steps, 1));
-      if (P.seg_ctas > 0)
-        // after a captured chunk of segmented steps row S->next is still to be sampled
-        TRY(forward_steps_seg(ctx, P, S->W, S->next, stop, S->q, &S->src, S->d, S->nr > 0 ? &S->rec : nullptr, s,
-                              &S->seg, S->exec != nullptr && S->next > 0));
-      else
-        TRY(forward_steps(ctx, P, S->W, S->next, stop, S->q, &S->src, S->d, S->nr > 0 ? &S->rec : nullptr,
-                          nullptr, 0, 0, s));
+      TRY(forward_steps(ctx, P, S->W, S->next, stop, S->q, &S->src, S->d, S->nr > 0 ? &S->rec : nullptr, nullptr,
+                        0, 0, s));
       steps -= stop - S->next;
       S->next = stop;
     }

@@ -355,11 +355,6 @@ struct SegWork {
   const float* inj_vals;   // source row n, or null
   GatherSet rec;
   float* rec_out;          // receiver row n, or null
-  // graph-replayed steps: the rows above are rows 0 of their arrays, and
-  // row n = *row_counter + row_offset, row_stride floats apart (null: as given)
-  const int* row_counter;
-  int row_offset;
-  long long inj_stride, rec_stride;
 };
 // Segmented plain step (3D) of `ctas` CTAs; the variant of p.iso.
 cudaError_t launch_step_seg(int R, bool iso, const StepMaps& maps, const StepParams& p, const SegWork& w, int ctas,

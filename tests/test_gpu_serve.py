@@ -130,12 +130,12 @@ def test_batched_advance_rejects_foreign_sessions(ctx):
         b.close()
 
 
-def test_concurrent_sessions_with_segmented_tails(ctx):
-    """Two resident 3D sessions on their own streams, both enqueued in full
-    before either is read: the steps outside captured chunks take the
-    segmented step, whose run starts and source-cell lists each session keeps
-    for itself.  The shorter request's tail runs while the longer one's is
-    still queued; each result equals wave_forward alone, bit for bit."""
+def test_concurrent_sessions_enqueued_in_full(ctx):
+    """Two resident 3D sessions of different grids and orders on their own
+    streams, both enqueued in full (captured chunks and the ragged tail) before
+    either is read, the shorter one finishing while the longer one's launches
+    are still queued: nothing one session's launches read is written by the
+    other's, and each result equals wave_forward alone, bit for bit."""
     dev = torch.device("cuda", 0)
     reqs = [dict(id=0, ndim=3, N=66, h=10.0, nbl=8, so=8, nt=250, n_layers=5, n_rec=80, model_seed=7, f0=0.015),
             dict(id=1, ndim=3, N=41, h=10.0, nbl=8, so=16, nt=60, n_layers=4, n_rec=50, model_seed=8, f0=0.015)]
@@ -143,8 +143,7 @@ def test_concurrent_sessions_with_segmented_tails(ctx):
     sess = []
     for r, st in zip(reqs, streams):
         geom, m, src, q, rec, dt = request_problem(r, dev)
-        # both grids take column segments outside the captured chunks
-        assert (r["nt"] - 1) % 32 != 0
+        assert (r["nt"] - 1) % 32 != 0  # a ragged tail after the captured chunks
         torch.cuda.synchronize()
         sess.append(wave.Session(ctx, geom, m, src, q, rec, dt, r["nt"], r["so"],
                                  stream=wave.ctypes.c_void_p(st.cuda_stream), graph_chunk=32))
