@@ -168,13 +168,15 @@ struct StepLayout {
   //    0.710 -> 0.667 ms, 16-bit imaging steps 4-6 % faster) and the
   //    equal-spacing kernels from radius 7 (order 16 forward 0.934 -> 0.837 ms);
   //  * none where a group spills under the register cap (imaging at radius 5,
-  //    16-bit snapshot, imaging and Born steps at radius 6, general spacing
-  //    from radius 7) and for the paired planes of the deep steps up to
-  //    radius 2 (no measurable difference there).
+  //    16-bit snapshot, imaging and Born steps at radius 6 with general
+  //    spacing, general spacing from radius 7) and for the paired planes of
+  //    the deep steps up to radius 2 (no measurable difference there); the
+  //    equal-spacing radius-6 kernels, at 128 registers, take groups (order 12
+  //    FP16 snapshot step 0.722 -> 0.658 ms, FP16 imaging 0.871 -> 0.850 ms).
   static constexpr int UR_BASE =
       (NDIM != 3 || QU != 1) ? 1
       : (R >= kLeadMinR) ? (ISO ? kRenameGroup : 1)
-      : ((R == 5 && mode_is_grad(MODE)) || (R == 6 && MODE >= MODE_SNAP_BF16)) ? 1
+      : ((R == 5 && mode_is_grad(MODE)) || (R == 6 && MODE >= MODE_SNAP_BF16 && !ISO)) ? 1
       : ((DEEP && (R == 3 || R == 4)) || (R == 4 && MODE == MODE_GRAD_F32)) ? 2 * R + 1
       : kRenameGroup;
   // Lead-plane layouts take one stage per plane for both rings: stage s holds

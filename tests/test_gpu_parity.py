@@ -143,7 +143,7 @@ def _check_16bit(case, fmt, g, og, m, dt, nt, so, q, src, rec, d_obs):
     assert e_plain <= TOL_16BIT[fmt]
 
 
-@pytest.mark.parametrize("so,iso", [(10, False), (12, False), (14, True), (16, True)])
+@pytest.mark.parametrize("so,iso", [(10, False), (12, False), (12, True), (14, True), (16, True)])
 @pytest.mark.parametrize("fmt", ["fp16", "bf16"])
 def test_gradient_16bit_snapshots_high_order(ctx, so, iso, fmt):
     og, m, dt, nt, so, src, q, rec = small3d(so, spacing=(12.5, 12.5, 12.5) if iso else (10.0, 12.0, 9.0))
