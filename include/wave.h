@@ -444,10 +444,9 @@ WAVE_API int wave_ricker(float* q_out, int nt, float dt, float f0, float t0);
  *   stream:   CUDA stream (NULL = legacy default); the call copies phi to the
  *             host and returns after the stream has completed its work.
  * The first call on a device looks up the scratch array's device address (with
- * that device current); make that first call before any stream capture.  The
- * address is kept per device together with the id of the CUDA context it was
- * found in: after a device reset (cudaDeviceReset) the next call sees a new
- * context and looks the address up again.
+ * that device current).  The address is kept per device together with the id
+ * of the CUDA context it was found in: after a device reset (cudaDeviceReset)
+ * the next call sees a new context and looks the address up again.
  * Every call on a device shares the same scratch and overwrites it; calls that
  * overlap on the GPU (other streams, other host threads) race and must be
  * serialised by the caller.  Nothing in the scratch needs to start at zero.
