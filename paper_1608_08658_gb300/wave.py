@@ -176,6 +176,41 @@ def _f32(x):
     return np.ascontiguousarray(x, dtype=np.float32)
 
 
+def _numel(x):
+    return int(x.numel()) if _is_torch(x) else int(x.size)
+
+
+def _sized(name, x, shape):
+    """An input array as contiguous float32 holding exactly prod(shape)
+    elements (the library reads that many): checked before any call, so a
+    short array raises instead of being read past its end."""
+    x = _f32(x)
+    n = int(np.prod(shape))
+    if _numel(x) != n:
+        raise ValueError("%s has %d elements, expected %d %s" % (name, _numel(x), n, tuple(shape)))
+    return x
+
+
+def _out(name, x, shape, ref):
+    """A caller-supplied output buffer (float32, contiguous, exactly
+    prod(shape) elements: the library writes that many), or a new one of the
+    kind of `ref` when x is None."""
+    if x is None:
+        return _empty_like_kind(ref, shape)
+    if _is_torch(x):
+        import torch
+        if x.dtype != torch.float32:
+            raise TypeError("%s must be float32, got %s" % (name, x.dtype))
+        if not x.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    elif not isinstance(x, np.ndarray) or x.dtype != np.float32 or not x.flags["C_CONTIGUOUS"]:
+        raise TypeError("%s must be a C-contiguous float32 numpy array or torch tensor" % name)
+    n = int(np.prod(shape))
+    if _numel(x) != n:
+        raise ValueError("%s has %d elements, expected %d %s" % (name, _numel(x), n, tuple(shape)))
+    return x
+
+
 def _empty_like_kind(ref, shape):
     if ref is not None and _is_torch(ref):
         import torch
@@ -334,8 +369,8 @@ class Session:
         ps, self._src = _points(src, geom.ndim)
         pr, self._rec = _points(rec, geom.ndim)
         self.n_rec = int(pr.n)
-        m = _f32(m)
-        q = _f32(q) if ps.n else None
+        m = _sized("m", m, geom.phys_array_shape)
+        q = _sized("q", q, (self.nt, ps.n)) if ps.n else None
         h = ctypes.c_void_p()
         st = stream if stream is not None else _stream_for(m, q)
         rc = lib().wave_session_create(ctx.handle, ctypes.byref(h), ctypes.byref(g), _ptr(m), ctypes.byref(ps),
@@ -359,6 +394,7 @@ class Session:
     def read(self, out=None):
         if out is None:
             out = np.empty((self.nt, self.n_rec), dtype=np.float32)
+        out = _out("out", out, (self.nt, self.n_rec), None)
         _check(self.ctx, lib().wave_session_read(self.handle, _ptr(out) if self.n_rec else None))
         return out
 
@@ -408,14 +444,14 @@ def wave_forward(ctx, geom, m, src, q, rec, dt, nt, space_order, d_out=None, str
                  u_init_prev=None, u_init=None, return_final=False):
     """Receiver data [nt][n_rec] of the forward model (Listing 1).  With
     ``return_final`` also returns (u^{nt-2}, u^{nt-1}) on the computational grid."""
-    m = _f32(m)
+    m = _sized("m", m, geom.phys_array_shape)
     g = geom.to_c()
     ps, src_c = _points(src, geom.ndim)
     pr, rec_c = _points(rec, geom.ndim)
-    q = _f32(q) if ps.n else None
-    if d_out is None:
-        d_out = _empty_like_kind(m, (nt, pr.n))
-    ui_p, ui = _f32(u_init_prev), _f32(u_init)
+    q = _sized("q", q, (nt, ps.n)) if ps.n else None
+    d_out = _out("d_out", d_out, (nt, pr.n), m)
+    ui_p = None if u_init_prev is None else _sized("u_init_prev", u_init_prev, geom.comp_array_shape)
+    ui = None if u_init is None else _sized("u_init", u_init, geom.comp_array_shape)
     fin_p = fin = None
     if return_final:
         fin_p = _empty_like_kind(m, geom.comp_array_shape)
@@ -430,13 +466,12 @@ def wave_forward(ctx, geom, m, src, q, rec, dt, nt, space_order, d_out=None, str
 
 def wave_adjoint(ctx, geom, m, src, rec, y, dt, nt, space_order, q_out=None, stream=None):
     """Source-side traces F^T y [nt][n_src] (Listing 2 as the transpose)."""
-    m = _f32(m)
+    m = _sized("m", m, geom.phys_array_shape)
     g = geom.to_c()
     ps, src_c = _points(src, geom.ndim)
     pr, rec_c = _points(rec, geom.ndim)
-    y = _f32(y) if pr.n else None
-    if q_out is None:
-        q_out = _empty_like_kind(m, (nt, ps.n))
+    y = _sized("y", y, (nt, pr.n)) if pr.n else None
+    q_out = _out("q_out", q_out, (nt, ps.n), m)
     st = stream if stream is not None else _stream_for(m, y, q_out)
     rc = lib().wave_adjoint(ctx.handle, ctypes.byref(g), _ptr(m), ctypes.byref(ps), ctypes.byref(pr), _ptr(y),
                             _ptr(q_out) if ps.n else None, ctypes.c_float(dt), int(nt), int(space_order), st)
@@ -448,14 +483,13 @@ def wave_gradient(ctx, geom, m, src, q, rec, d_obs, dt, nt, space_order, snap_mo
                   grad_out=None, return_residual=False, stream=None):
     """(grad, phi[, residual]) of the objective of Eq. 2 by Eq. 3."""
     mode = SNAP_MODES[snap_mode] if isinstance(snap_mode, str) else int(snap_mode)
-    m = _f32(m)
+    m = _sized("m", m, geom.phys_array_shape)
     g = geom.to_c()
     ps, src_c = _points(src, geom.ndim)
     pr, rec_c = _points(rec, geom.ndim)
-    q = _f32(q) if ps.n else None
-    d_obs = _f32(d_obs) if pr.n else None
-    if grad_out is None:
-        grad_out = _empty_like_kind(m, geom.phys_array_shape)
+    q = _sized("q", q, (nt, ps.n)) if ps.n else None
+    d_obs = _sized("d_obs", d_obs, (nt, pr.n)) if pr.n else None
+    grad_out = _out("grad_out", grad_out, geom.phys_array_shape, m)
     resid = _empty_like_kind(m, (nt, pr.n)) if return_residual else None
     phi = ctypes.c_double()
     st = stream if stream is not None else _stream_for(m, q, d_obs, grad_out)
@@ -472,14 +506,15 @@ def wave_jacobian_adjoint(ctx, geom, m, src, q, rec, y, dt, nt, space_order, sna
                           grad_out=None, d_out=None, stream=None):
     """J^T y for the map m -> receiver data (the residual replaced by y)."""
     mode = SNAP_MODES[snap_mode] if isinstance(snap_mode, str) else int(snap_mode)
-    m = _f32(m)
+    m = _sized("m", m, geom.phys_array_shape)
     g = geom.to_c()
     ps, src_c = _points(src, geom.ndim)
     pr, rec_c = _points(rec, geom.ndim)
-    q = _f32(q) if ps.n else None
-    y = _f32(y) if pr.n else None
-    if grad_out is None:
-        grad_out = _empty_like_kind(m, geom.phys_array_shape)
+    q = _sized("q", q, (nt, ps.n)) if ps.n else None
+    y = _sized("y", y, (nt, pr.n)) if pr.n else None
+    grad_out = _out("grad_out", grad_out, geom.phys_array_shape, m)
+    if d_out is not None:
+        d_out = _out("d_out", d_out, (nt, pr.n), m)
     st = stream if stream is not None else _stream_for(m, q, y, grad_out)
     rc = lib().wave_jacobian_adjoint(ctx.handle, ctypes.byref(g), _ptr(m), ctypes.byref(ps), _ptr(q),
                                      ctypes.byref(pr), _ptr(y), _ptr(grad_out), _ptr(d_out) if pr.n else None,
@@ -491,7 +526,7 @@ def wave_jacobian_adjoint(ctx, geom, m, src, q, rec, y, dt, nt, space_order, sna
 def wave_gradient_shots(ctx, geom, m, shots, dt, nt, space_order, snap_mode="auto", grad_out=None, stream=None):
     """(sum of gradients, sum of objectives) over ``shots`` = [(src, q, rec, d_obs), ...]."""
     mode = SNAP_MODES[snap_mode] if isinstance(snap_mode, str) else int(snap_mode)
-    m = _f32(m)
+    m = _sized("m", m, geom.phys_array_shape)
     g = geom.to_c()
     n = len(shots)
     srcs = (c_points * n)()
@@ -502,12 +537,12 @@ def wave_gradient_shots(ctx, geom, m, shots, dt, nt, space_order, snap_mode="aut
     for i, (src, q, rec, d_obs) in enumerate(shots):
         ps, sc = _points(src, geom.ndim)
         pr, rc_ = _points(rec, geom.ndim)
-        qf, df = _f32(q), _f32(d_obs)
+        qf = _sized("q of shot %d" % i, q, (nt, ps.n)) if ps.n else None
+        df = _sized("d_obs of shot %d" % i, d_obs, (nt, pr.n)) if pr.n else None
         keep += [sc, rc_, qf, df]
         srcs[i], recs[i] = ps, pr
         qs[i], obs[i] = _ptr(qf), _ptr(df)
-    if grad_out is None:
-        grad_out = _empty_like_kind(m, geom.phys_array_shape)
+    grad_out = _out("grad_out", grad_out, geom.phys_array_shape, m)
     phi = ctypes.c_double()
     st = stream if stream is not None else _stream_for(m, grad_out)
     rc = lib().wave_gradient_shots(ctx.handle, ctypes.byref(g), _ptr(m), n, srcs, qs, recs, obs, _ptr(grad_out),
@@ -519,14 +554,13 @@ def wave_gradient_shots(ctx, geom, m, shots, dt, nt, space_order, snap_mode="aut
 
 def wave_born(ctx, geom, m, dm, src, q, rec, dt, nt, space_order, d_out=None, stream=None):
     """Linearised data J dm [nt][n_rec] (derivative of wave_forward's data in m)."""
-    m = _f32(m)
-    dm = _f32(dm)
+    m = _sized("m", m, geom.phys_array_shape)
+    dm = _sized("dm", dm, geom.phys_array_shape)
     g = geom.to_c()
     ps, src_c = _points(src, geom.ndim)
     pr, rec_c = _points(rec, geom.ndim)
-    q = _f32(q) if ps.n else None
-    if d_out is None:
-        d_out = _empty_like_kind(m, (nt, pr.n))
+    q = _sized("q", q, (nt, ps.n)) if ps.n else None
+    d_out = _out("d_out", d_out, (nt, pr.n), m)
     st = stream if stream is not None else _stream_for(m, dm, q, d_out)
     rc = lib().wave_born(ctx.handle, ctypes.byref(g), _ptr(m), _ptr(dm), ctypes.byref(ps), _ptr(q),
                          ctypes.byref(pr), _ptr(d_out) if pr.n else None, ctypes.c_float(dt), int(nt),
@@ -617,8 +651,7 @@ def wave_column_runs_for(columns, nz, chunks, space_order, slots=304, force=Fals
 def wave_ricker(nt, dt, f0, t0=None, out=None):
     if t0 is None:
         t0 = 1.0 / f0
-    if out is None:
-        out = np.empty(nt, dtype=np.float32)
+    out = _out("out", out, (int(nt),), None)
     rc = lib().wave_ricker(_ptr(out), int(nt), ctypes.c_float(dt), ctypes.c_float(f0), ctypes.c_float(t0))
     if rc != WAVE_OK:
         raise WaveError(rc, "bad arguments to wave_ricker")
