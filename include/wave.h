@@ -79,9 +79,10 @@ typedef struct wave_context wave_context;
  * parameter (not derived from m) so that eta does not depend on the model. */
 typedef struct {
   int32_t ndim;          /* 2 or 3 */
-  int32_t nbl;           /* absorbing points per side, >= 0 */
+  int32_t nbl;           /* absorbing points per side, in [0, 2^20] */
   int64_t shape[3];      /* physical points per axis, x-first, each in [2, 2^20]
-                            (WAVE_ERR_INVALID_ARG otherwise); shape[2] ignored in 2D.
+                            (WAVE_ERR_INVALID_ARG otherwise, and for a computational
+                            grid above 2^40 points); shape[2] ignored in 2D.
                             A grid whose axis 1 needs more than 65535 CTA tiles of 14-16
                             rows is WAVE_ERR_NOT_SUPPORTED. */
   double spacing[3];     /* grid spacing per axis, m, > 0 */

@@ -496,15 +496,22 @@ int prepare(wave_context* ctx, const wave_geometry* geom, float dt, int nt, int 
   if (!valid_order(so)) return fail(ctx, WAVE_ERR_INVALID_ARG, "space_order must be even in [2, 16], got %d", so);
   if (nt < 2) return fail(ctx, WAVE_ERR_INVALID_ARG, "nt must be >= 2, got %d", nt);
   if (!(dt > 0.f) || !std::isfinite(dt)) return fail(ctx, WAVE_ERR_INVALID_ARG, "dt must be positive and finite");
-  if (geom->nbl < 0) return fail(ctx, WAVE_ERR_INVALID_ARG, "nbl must be >= 0");
+  if (geom->nbl < 0 || geom->nbl > (1 << 20))
+    return fail(ctx, WAVE_ERR_INVALID_ARG, "nbl = %d out of range [0, 2^20]", geom->nbl);
   if (geom->nbl > 0 && !(geom->sponge_vref > 0)) return fail(ctx, WAVE_ERR_INVALID_ARG, "sponge_vref must be > 0");
   const int nd = geom->ndim;
+  double points = 1.0;  // computational points, in double so that no product overflows
   for (int d = 0; d < nd; ++d) {
     if (geom->shape[d] < 2 || geom->shape[d] > (1 << 20))
       return fail(ctx, WAVE_ERR_INVALID_ARG, "shape[%d] = %lld out of range [2, 2^20]", d, (long long)geom->shape[d]);
     if (!(geom->spacing[d] > 0) || !std::isfinite(geom->spacing[d]))
       return fail(ctx, WAVE_ERR_INVALID_ARG, "spacing[%d] must be positive", d);
+    points *= double(geom->shape[d] + 2 * static_cast<long long>(geom->nbl) + 8);
   }
+  // far beyond any device memory; the bound keeps every element count below
+  // in 64-bit range
+  if (points > 1099511627776.0)
+    return fail(ctx, WAVE_ERR_INVALID_ARG, "computational grid of %.3g points exceeds 2^40", points);
   P->ndim = nd;
   P->so = so;
   P->R = so / 2;

@@ -79,3 +79,23 @@ def test_empty_point_set():
     _, g = _geoms(og)
     idx, w = wave.wave_interpolation_operator(g, np.zeros((0, 3), dtype=np.float32))
     assert idx.shape == (0, 8) and w.shape == (0, 8)
+
+
+@pytest.mark.parametrize("shape,nbl", [((20, 20, 20), (1 << 20) + 1),                 # layer beyond 2^20 points
+                                       ((1 << 20, 1 << 20, 1 << 20), 0),               # 2^60 points
+                                       ((1 << 14, 1 << 14, 1 << 12), 40)])             # just above 2^40
+def test_geometry_beyond_the_size_bounds_is_rejected(shape, nbl):
+    """Geometry checks of the host-side set-up: the absorbing layer and the
+    computational grid's point count are bounded before any size is formed, so
+    no element count can overflow."""
+    geom = wave.Geometry(shape=shape, spacing=(10.0, 10.0, 10.0), nbl=nbl, sponge_vref=2.0)
+    with pytest.raises(wave.WaveError) as e:
+        wave.wave_interpolation_operator(geom, np.array([[15.0, 15.0, 15.0]], np.float32))
+    assert e.value.code == wave.WAVE_ERR_INVALID_ARG
+
+
+def test_large_but_bounded_geometry_is_accepted():
+    # 2^13 x 2^13 x 2^13 physical points (+ 2 x 40): below the 2^40 bound; nothing is allocated
+    geom = wave.Geometry(shape=(1 << 13,) * 3, spacing=(10.0, 10.0, 10.0), nbl=40, sponge_vref=2.0)
+    idx, wts = wave.wave_interpolation_operator(geom, np.array([[15.0, 15.0, 15.0]], np.float32))
+    assert idx.shape == (1, 8) and abs(float(wts.sum()) - 1.0) < 1e-6
