@@ -95,7 +95,8 @@ typedef struct {
  * or device pointer).  Interpolation (Sec. IV, sparse-point interpolation):
  * per axis t = (p - o)/h on the computational grid, i = floor(t), f = t - i,
  * (i = n-2, f = 1 on the last node); corner weights are products of (1-f, f).
- * Every point must lie inside the physical domain (WAVE_ERR_POINT_OUTSIDE). */
+ * Every point must lie inside the physical domain (WAVE_ERR_POINT_OUTSIDE).
+ * n is in [0, 2^28) (WAVE_ERR_INVALID_ARG otherwise). */
 typedef struct {
   int64_t n;
   const float* coords;
@@ -410,7 +411,7 @@ WAVE_API int wave_fd_weights(int space_order, double* w_out);
  *     (n_d = N_d + 2 nbl);
  *   weight_out: pts->n * 2^ndim float32 weights; entry c of a point is the
  *     cell corner whose axis-a index is the upper one when bit a of c is set.
- * Errors: INVALID_ARG (NULL pointer, bad geometry, n < 0 or n > 2^28);
+ * Errors: INVALID_ARG (NULL pointer, bad geometry, n < 0 or n >= 2^28);
  * POINT_OUTSIDE (a point outside the physical domain). */
 WAVE_API int wave_interpolation_operator(const wave_geometry* geom, const wave_points* pts, int64_t* index_out,
                                          float* weight_out);

@@ -740,7 +740,9 @@ struct PointsHost {
 int read_points(wave_context* ctx, Prob& P, const wave_points* pts, std::vector<float>* c, uint64_t* key_out) {
   if (!pts) return fail(ctx, WAVE_ERR_INVALID_ARG, "point set is NULL");
   const long long n = pts->n;
-  if (n < 0 || n > (1LL << 28)) return fail(ctx, WAVE_ERR_INVALID_ARG, "point count %lld out of range", n);
+  // below 2^28 so that the 2^ndim corner entries of all points stay within
+  // the 32-bit row pointers of the injection structure
+  if (n < 0 || n >= (1LL << 28)) return fail(ctx, WAVE_ERR_INVALID_ARG, "point count %lld out of range [0, 2^28)", n);
   if (n > 0 && !pts->coords) return fail(ctx, WAVE_ERR_INVALID_ARG, "point coordinates are NULL");
   c->resize(static_cast<size_t>(n) * P.ndim);
   if (n > 0) {
@@ -2377,7 +2379,7 @@ int wave_session_destroy(wave_session* S) {
 
 int wave_interpolation_operator(const wave_geometry* geom, const wave_points* pts, int64_t* index_out,
                                 float* weight_out) {
-  if (!geom || !pts || pts->n < 0 || pts->n > (1LL << 28) || (pts->n > 0 && (!pts->coords || !index_out || !weight_out)))
+  if (!geom || !pts || pts->n < 0 || pts->n >= (1LL << 28) || (pts->n > 0 && (!pts->coords || !index_out || !weight_out)))
     return WAVE_ERR_INVALID_ARG;
   Prob P;
   // the time step and order do not enter the interpolation

@@ -99,3 +99,21 @@ def test_large_but_bounded_geometry_is_accepted():
     geom = wave.Geometry(shape=(1 << 13,) * 3, spacing=(10.0, 10.0, 10.0), nbl=40, sponge_vref=2.0)
     idx, wts = wave.wave_interpolation_operator(geom, np.array([[15.0, 15.0, 15.0]], np.float32))
     assert idx.shape == (1, 8) and abs(float(wts.sum()) - 1.0) < 1e-6
+
+
+def test_point_count_bound_is_exclusive():
+    """2^28 points would give 2^31 corner entries in 3D, one past the 32-bit
+    row pointers of the injection structure: rejected before the coordinates
+    are read (the call gets a one-point buffer that it never touches)."""
+    import ctypes
+    geom = wave.Geometry(shape=(20, 20, 20), spacing=(10.0, 10.0, 10.0), nbl=4, sponge_vref=2.0)
+    g = geom.to_c()
+    one = np.zeros(3, np.float32)
+    idx = np.zeros(8, np.int64)
+    wts = np.zeros(8, np.float32)
+    for n, want in (((1 << 28), wave.WAVE_ERR_INVALID_ARG), ((1 << 28) + 5, wave.WAVE_ERR_INVALID_ARG),
+                    (1, wave.WAVE_OK)):
+        pts = wave.c_points(n, one.ctypes.data)
+        rc = wave.lib().wave_interpolation_operator(ctypes.byref(g), ctypes.byref(pts), idx.ctypes.data,
+                                                    wts.ctypes.data)
+        assert rc == want, (n, rc)
