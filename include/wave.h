@@ -205,6 +205,17 @@ WAVE_API int wave_context_set_column_segments(wave_context* ctx, int mode);
 WAVE_API int wave_column_runs_for(long long columns, int nz, int chunks, int space_order, long long slots, int force,
                                   long long* run_start, int cap, int* n_runs);
 
+/* Host-only: the number of chunks the streamed axis of the plain 3D step is cut
+ * into for a grid of `columns` column tiles of nz planes with `slots` resident
+ * CTAs (the z-chunk grid has columns * chunks CTAs).  Chunks keep at least
+ * max(32, 4R) planes; where that still allows 8 waves of CTAs, the count is
+ * the one, among those giving 8 to 16 waves, whose last wave is fullest (the
+ * smallest within 1 % of the best), else the most chunks allowed.
+ *   chunks: out, the number of chunks (>= 1).
+ * Errors: INVALID_ARG (columns, nz or slots < 1, space_order not even in
+ * [2, 16], chunks NULL). */
+WAVE_API int wave_z_chunks_for(long long columns, int nz, int space_order, long long slots, int* chunks);
+
 /* Test hook of the same failure-detection path (no counterpart in the paper):
  * the context's next stencil-step launch issues none of its tile loads, so
  * every wait of its consumer warps runs out after the wait limit, the kernel

@@ -2434,6 +2434,12 @@ int wave_column_runs_for(long long columns, int nz, int chunks, int space_order,
   return WAVE_OK;
 }
 
+int wave_z_chunks_for(long long columns, int nz, int space_order, long long slots, int* chunks) {
+  if (columns < 1 || nz < 1 || slots < 1 || !valid_order(space_order) || !chunks) return WAVE_ERR_INVALID_ARG;
+  *chunks = choose_chunks(columns, nz, space_order / 2, slots);
+  return WAVE_OK;
+}
+
 int wave_context_storage_plan(const wave_context* ctx, int* levels, int* parts, int* segments) {
   if (!ctx) return WAVE_ERR_INVALID_ARG;
   if (levels) *levels = ctx->last_plan[1];

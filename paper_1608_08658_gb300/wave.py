@@ -73,6 +73,8 @@ _SIGS = {
     "wave_column_runs_for": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_longlong, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong),
                                             ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "wave_z_chunks_for": (ctypes.c_int, [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_longlong,
+                                         ctypes.POINTER(ctypes.c_int)]),
     "wave_error_string": (ctypes.c_char_p, [ctypes.c_int]),
     "wave_last_error": (ctypes.c_char_p, [_P]),
     "wave_forward": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, ctypes.c_float, ctypes.c_int, ctypes.c_int, _P]),
@@ -646,6 +648,15 @@ def wave_column_runs_for(columns, nz, chunks, space_order, slots=304, force=Fals
     if rc != WAVE_OK:
         raise WaveError(rc, "bad arguments to wave_column_runs_for")
     return np.array(buf[:n.value + 1], dtype=np.int64) if n.value else None
+
+
+def wave_z_chunks_for(columns, nz, space_order, slots=304):
+    """Host-only: chunks per column of the z-chunk grid of the plain 3D step."""
+    c = ctypes.c_int()
+    rc = lib().wave_z_chunks_for(int(columns), int(nz), int(space_order), int(slots), ctypes.byref(c))
+    if rc != WAVE_OK:
+        raise WaveError(rc, "bad arguments to wave_z_chunks_for")
+    return int(c.value)
 
 
 def wave_ricker(nt, dt, f0, t0=None, out=None):

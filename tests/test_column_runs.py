@@ -69,3 +69,38 @@ def test_bad_arguments_are_rejected():
         with pytest.raises(wave.WaveError) as e:
             wave.wave_column_runs_for(*args)
         assert e.value.code == wave.WAVE_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("columns,nz,so,want", [
+    (370, 592, 8, 9),     # 592^3 at order 8: 10 x 37 columns of 64 x 16, measured best of 1..9 chunks
+    (430, 592, 16, 7),    # 592^3 at order 16 (equal spacing): 10 x 43 columns of 64 x 14
+    (105, 150, 14, 4),    # the paper's demo shape: 8 waves out of reach, the most chunks of >= 32 planes
+    (6, 20, 8, 1),        # fewer planes than one chunk's minimum: one chunk
+])
+def test_z_chunks_follow_the_wave_rule(columns, nz, so, want):
+    """The z-chunk count of the plain 3D step on 152 SMs x 2 resident CTAs: at
+    least 8 waves where chunks of max(32, 4R) planes allow it, then the count
+    up to 16 waves whose last wave is fullest."""
+    assert wave.wave_z_chunks_for(columns, nz, so, 304) == want
+
+
+def test_z_chunks_properties():
+    slots = 304
+    for so in (2, 8, 16):
+        R = so // 2
+        for columns in (1, 7, 50, 144, 370, 1200):
+            for nz in (10, 64, 150, 592, 1000):
+                c = wave.wave_z_chunks_for(columns, nz, so, slots)
+                cmax = max(1, nz // max(32, 4 * R))
+                assert 1 <= c <= cmax
+                if columns * cmax < 8 * slots:
+                    assert c == cmax                        # short of 8 waves: as many chunks as allowed
+                else:
+                    lo = -(-8 * slots // columns)           # fewest chunks giving 8 waves
+                    assert lo <= c <= min(cmax, 2 * lo)
+
+
+def test_z_chunks_bad_arguments():
+    for args in ((0, 10, 8, 304), (10, 0, 8, 304), (10, 10, 7, 304), (10, 10, 8, 0)):
+        with pytest.raises(wave.WaveError):
+            wave.wave_z_chunks_for(*args)
