@@ -30,6 +30,9 @@
  *         library detects which and stages host arrays through its own
  *         workspace.  The caller owns all argument buffers; the context owns
  *         its workspace (wavefields, coefficients, snapshots, checkpoints).
+ *         Each array must hold the elements documented for its argument: a
+ *         raw pointer carries no size, so the library cannot check it (the
+ *         Python binding checks every array before the call).
  * Streams: work is enqueued on the CUDA stream passed as `stream`
  *         (cudaStream_t cast to void*, NULL = legacy default stream).  Every
  *         compute entry point returns after that stream has completed the
